@@ -126,7 +126,7 @@ def _min_block_photon(g, blocks, a):
 _LET = _string.ascii_letters
 
 
-def _chain(items, pairs, out_free):
+def _chain(items, pairs, out_free, Bn=1):
     """Product items[-1] ... items[0] of 4x4 factors.
 
     items: list of (array, labels) where array is [B,4,4] ('b' batch) or
@@ -161,8 +161,12 @@ def _chain(items, pairs, out_free):
         s += row + col
         ops.append(arr)
         subs.append(s)
-    out = "Z" + "".join(out_free) + bond[L] + bond[0]
-    return np.einsum(",".join(subs) + "->" + out, *ops, optimize="greedy")
+    any_batch = any("Z" in s for s in subs)
+    out = ("Z" if any_batch else "") + "".join(out_free) + bond[L] + bond[0]
+    r = np.einsum(",".join(subs) + "->" + out, *ops, optimize="greedy")
+    if not any_batch:
+        r = np.broadcast_to(r, (Bn,) + r.shape).copy()
+    return r
 
 
 def _pairings(idx):
@@ -369,7 +373,7 @@ class TermEvaluator:
             for k, o in seq)
         if bl.proj in ("F2", "L", "UV"):
             assert has_mu
-            G = _chain(self._items(bl, seq, mom, contracted, Bn), pairs, ["M"])
+            G = _chain(self._items(bl, seq, mom, contracted, Bn), pairs, ["M"], Bn)
             if bl.proj == "L":
                 return np.real(dirac.l_of_vertex(G))
             if bl.proj == "UV":
@@ -378,17 +382,17 @@ class TermEvaluator:
             for (t, eta, A, C, K, minus) in mom:
                 if t in contracted or np.all(C == 0.0):
                     continue
-                H = H + _chain(self._items(bl, seq, mom, contracted, Bn, (t, "q")), pairs, ["M", "J"])
+                H = H + _chain(self._items(bl, seq, mom, contracted, Bn, (t, "q")), pairs, ["M", "J"], Bn)
             return np.real(dirac.f2_of_vertex(G, H))
         if bl.proj == "SEmass":
-            S = _chain(self._items(bl, seq, mom, contracted, Bn), pairs, [])
+            S = _chain(self._items(bl, seq, mom, contracted, Bn), pairs, [], Bn)
             return np.real(0.5 * np.trace(S[:, 0:2, 0:2], axis1=-2, axis2=-1))
         if bl.proj == "SEwf":
             D = np.zeros((Bn, 4, 4, 4), dtype=complex)
             for (t, eta, A, C, K, minus) in mom:
                 if t in contracted or np.all(K == 0.0):
                     continue
-                D = D + _chain(self._items(bl, seq, mom, contracted, Bn, (t, "k")), pairs, ["N"])
+                D = D + _chain(self._items(bl, seq, mom, contracted, Bn, (t, "k")), pairs, ["N"], Bn)
             acc = 0.0
             for nu in range(4):
                 acc = acc + dirac.METRIC[nu] * np.trace(dirac.GAMMA[nu] @ D[:, nu], axis1=-2, axis2=-1)
