@@ -393,9 +393,10 @@ class TermEvaluator:
                 if t in contracted or np.all(K == 0.0):
                     continue
                 D = D + _chain(self._items(bl, seq, mom, contracted, Bn, (t, "k")), pairs, ["N"], Bn)
+            # D[nu] = dSigma/dk^nu = b gamma_nu (lower index): tr(gamma^nu D_nu) = 16 b
             acc = 0.0
             for nu in range(4):
-                acc = acc + dirac.METRIC[nu] * np.trace(dirac.GAMMA[nu] @ D[:, nu], axis1=-2, axis2=-1)
+                acc = acc + np.trace(dirac.GAMMA[nu] @ D[:, nu], axis1=-2, axis2=-1)
             return np.real(acc / 16.0)
         raise ValueError(bl.proj)
 
