@@ -124,49 +124,62 @@ def _min_block_photon(g, blocks, a):
 # ---------------------------------------------------------------------------
 
 _LET = _string.ascii_letters
+_PAIR_LABELS = "abdefghiklmnopqtuvwxyABCDEFGHIKLOPQRSTUVWXY"
 
 
 def _chain(items, pairs, out_free, Bn=1):
-    """Product items[-1] ... items[0] of 4x4 factors.
+    """Product items[-1] ... items[0] of 4x4 factors, built right to left.
 
-    items: list of (array, labels) where array is [B,4,4] ('b' batch) or
-    [4,4] or [F,4,4] with a named free index; labels = (batch?, free-name or
-    None).  pairs: list of (i, j) item positions joined by one TCON.
-    out_free: names of free indices to keep in output order.
-    Returns array [B, *free, 4, 4].
+    items: list of (array, has_batch, free) where array is [B,4,4] (batch),
+    [4,4], or [F,4,4] / [B,F,4,4] carrying the named free index ``free``;
+    array None marks a gamma slot contracted with its partner in ``pairs``
+    (a Feynman-gauge photon or a contracted loop-momentum pair: sum over
+    alpha of gamma^alpha ... gamma_alpha).
+    Returns array [B, *out_free, 4, 4].
     """
-    L = len(items)
-    bond = [_LET[i] for i in range(L + 1)]   # bond[t] = column of item t
-    ops, subs = [], []
-    paired = {}
+    partner = {}
     for (i, j) in pairs:
-        paired[i] = (i, j)
-        paired[j] = (i, j)
-    done = set()
+        partner[i] = j
+        partner[j] = i
+    # R dims: [B, open axes..., 4, 4]; open axes are free indices or the
+    # alpha of a pair whose second gamma is still to come.
+    R = np.broadcast_to(np.eye(4, dtype=complex), (Bn, 4, 4)).copy()
+    names = []
+
+    def lmul(M, R, nb):
+        # M: [B?, F?, 4, 4] with nb = number of leading batch dims of M (0/1)
+        if nb:
+            M = M.reshape((M.shape[0],) + (1,) * len(names) + M.shape[1:])
+        return np.matmul(M, R) if M.ndim == R.ndim else np.matmul(M, R[..., None, :, :])
+
     for t, (arr, has_batch, free) in enumerate(items):
-        row, col = bond[t + 1], bond[t]
-        if arr is None:            # contracted gamma slot
-            i, j = paired[t]
-            if (i, j) in done:
+        if arr is None:
+            j = partner[t]
+            lab = _PAIR_LABELS[min(t, j)]
+            if j > t:      # open the pair: gamma^alpha, alpha as a new axis
+                R = np.matmul(GAMMA_STACK, R[..., None, :, :])
+                names.append(lab)
                 continue
-            done.add((i, j))
-            ops.append(dirac.TCON)
-            subs.append(bond[i + 1] + bond[i] + bond[j + 1] + bond[j])
+            k = names.index(lab)
+            Rk = np.moveaxis(R, 1 + k, -3)            # [..., alpha, 4, 4]
+            R = np.matmul(GAMMA_LOWER, Rk).sum(axis=-3)
+            names.pop(k)
             continue
-        s = ""
-        if has_batch:
-            s += "Z"
-        if free is not None:
-            s += free
-        s += row + col
-        ops.append(arr)
-        subs.append(s)
-    any_batch = any("Z" in s for s in subs)
-    out = ("Z" if any_batch else "") + "".join(out_free) + bond[L] + bond[0]
-    r = np.einsum(",".join(subs) + "->" + out, *ops, optimize="greedy")
-    if not any_batch:
-        r = np.broadcast_to(r, (Bn,) + r.shape).copy()
-    return r
+        if free is None:
+            if has_batch:
+                R = np.matmul(arr.reshape((arr.shape[0],) + (1,) * len(names) + (4, 4)), R)
+            else:
+                R = np.matmul(arr, R)
+        else:
+            if has_batch:
+                A = arr.reshape((arr.shape[0],) + (1,) * len(names) + arr.shape[1:])
+            else:
+                A = arr
+            R = np.matmul(A, R[..., None, :, :])
+            names.append(free)
+    assert sorted(names) == sorted(out_free), (names, out_free)
+    perm = [0] + [1 + names.index(f) for f in out_free] + [1 + len(names), 2 + len(names)]
+    return np.transpose(R, perm)
 
 
 def _pairings(idx):
