@@ -1,0 +1,744 @@
+// Integrand code generator (host C++, runs at build time).
+//
+// For every vertex graph of the requested loop orders it builds the
+// forest-like subtraction formula (Sec. 2: linear operators applied to the
+// amplitudes of UV-divergent subdiagrams; each graph's contribution is one
+// Feynman-parametric integral) and emits straight-line device code for the
+// subtracted integrand, templated on the scalar type so that the same source
+// serves the FP64 path and the double-double re-evaluation of flagged points
+// (Sec. 3: arithmetics of different precisions).
+//
+// Operator reading (the paper defers the definitions to its references):
+//   U on a vertex-like subgraph S: S at zero external momenta, c * gamma_mu;
+//   U on a self-energy S: on-shell mass part + (k-slash - m) * slope at k = 0;
+//   L on a vertex-like S: on-shell forward vertex constant;
+//   A on a vertex-like S containing X: F2(0) of S;
+//   A~_G = sum_F (-1)^|F| [ T(F;G) + sum_{G' in F, X in G'} T(F;G') ],
+//   T(F;G'): G' gets A, every element of F u {G} strictly containing G' gets
+//   (L - U), every other element gets U.
+// Every operator value is a block of the same Feynman parameters whose loop
+// momenta decouple from the enclosing loops (block-diagonal Lambda).
+//
+// Integrand of one term (Feynman gauge, m = 1, in units of (alpha/pi)^n):
+//   (-1)^n 4^-n sum_{k<n} (-1)^k Gamma(n-k) U^-2 V^(k-n) (2U)^-k
+//       sum_{k contractions} prod B_ij * projected Dirac string.
+//
+// Dirac coefficients: every factor of a string (gamma^mu in the Dirac
+// representation, p-slash = gamma^0 in the rest frame, the identity) has one
+// non-zero entry per row, so strings are multiplied as (column map, values)
+// pairs and projected with trace functionals Tr[W M].
+//
+// Usage: qed_gen <out.cu> <loop orders...>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <map>
+#include <set>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "qed_graph.hpp"
+
+using cd = std::complex<double>;
+using namespace qed;
+
+// ---------------------------------------------------------------------------
+// monomial 4x4 matrices
+// ---------------------------------------------------------------------------
+struct Mono {
+  int col[4];
+  cd val[4];
+};
+static Mono mono_identity() { Mono m; for (int r = 0; r < 4; ++r) { m.col[r] = r; m.val[r] = 1.0; } return m; }
+// a * b
+static Mono mono_mul(const Mono &a, const Mono &b) {
+  Mono m;
+  for (int r = 0; r < 4; ++r) { int c = a.col[r]; m.col[r] = b.col[c]; m.val[r] = a.val[r] * b.val[c]; }
+  return m;
+}
+static Mono GAM[4];          // gamma^mu
+static Mono GAM_LOW[4];      // gamma_mu
+static double METRIC[4] = {1, -1, -1, -1};
+typedef cd Dense[4][4];
+static void to_dense(const Mono &m, Dense &d) {
+  for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) d[r][c] = 0.0;
+  for (int r = 0; r < 4; ++r) d[r][m.col[r]] = m.val[r];
+}
+static void dense_mul(const Dense &a, const Dense &b, Dense &o) {
+  Dense t;
+  for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) { cd s = 0; for (int k = 0; k < 4; ++k) s += a[r][k] * b[k][c]; t[r][c] = s; }
+  for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) o[r][c] = t[r][c];
+}
+// Tr[W M] for dense W, monomial M
+static cd tr_wm(const Dense &W, const Mono &M) {
+  cd s = 0;
+  for (int r = 0; r < 4; ++r) s += W[M.col[r]][r] * M.val[r];
+  return s;
+}
+
+static void init_gammas() {
+  const cd I(0, 1);
+  Mono g0; for (int r = 0; r < 4; ++r) { g0.col[r] = r; g0.val[r] = r < 2 ? 1.0 : -1.0; }
+  // gamma^k = [[0, s_k], [-s_k, 0]]
+  cd s[3][2][2] = {{{0, 1}, {1, 0}}, {{0, -I}, {I, 0}}, {{1, 0}, {0, -1}}};
+  GAM[0] = g0;
+  for (int k = 0; k < 3; ++k) {
+    Mono m;
+    for (int r = 0; r < 2; ++r) for (int c = 0; c < 2; ++c)
+      if (std::abs(s[k][r][c]) > 0) { m.col[r] = 2 + c; m.val[r] = s[k][r][c]; m.col[2 + r] = c; m.val[2 + r] = -s[k][r][c]; }
+    GAM[k + 1] = m;
+  }
+  for (int mu = 0; mu < 4; ++mu) { GAM_LOW[mu] = GAM[mu]; for (int r = 0; r < 4; ++r) GAM_LOW[mu].val[r] *= METRIC[mu]; }
+}
+
+// Trace functionals used by the projections (rest frame, m = 1).
+static Dense W_F1;            // (1/4)(1 + gamma^0): charge / on-shell constant / mass part
+static Dense W_MAG_G[4];      // magnetic part from G^i (index mu = i)
+static Dense W_MAG_H[4][4];   // magnetic part from dG^i/dq^j
+static Dense W_UV[4];         // gamma_mu / 16
+static Dense W_WF[4];         // gamma^nu / 16
+static void init_projectors() {
+  const cd I(0, 1);
+  Dense one, g0, Pp, Sig[4], gj[4];
+  for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) one[r][c] = (r == c) ? 1.0 : 0.0;
+  to_dense(GAM[0], g0);
+  for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) { Pp[r][c] = 0.5 * (one[r][c] + g0[r][c]); W_F1[r][c] = 0.25 * (one[r][c] + g0[r][c]); }
+  for (int j = 1; j < 4; ++j) to_dense(GAM[j], gj[j]);
+  // Sigma^l = (i/2) eps_ljk gamma^j gamma^k = diag(s_l, s_l)
+  for (int l = 1; l < 4; ++l) {
+    int j = l % 3 + 1, k = (l + 1) % 3 + 1;
+    Dense a, b;
+    dense_mul(gj[j], gj[k], a);
+    dense_mul(gj[k], gj[j], b);
+    for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) Sig[l][r][c] = 0.5 * I * (a[r][c] - b[r][c]);
+  }
+  auto eps = [](int i, int j, int l) -> double {
+    if (i == j || j == l || i == l) return 0.0;
+    int p[3] = {i, j, l};
+    int inv = 0;
+    for (int x = 0; x < 3; ++x) for (int y = x + 1; y < 3; ++y) if (p[x] > p[y]) ++inv;
+    return inv % 2 ? -1.0 : 1.0;
+  };
+  for (int i = 0; i < 4; ++i) {
+    for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) W_MAG_G[i][r][c] = 0.0;
+    for (int j = 0; j < 4; ++j) for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) W_MAG_H[i][j][r][c] = 0.0;
+  }
+  // magnetic moment (F1+F2) = (i/6) sum eps_ijl Tr[P+ Sigma^l (H^i_j - [gamma^j, G^i]/4)]
+  for (int i = 1; i < 4; ++i)
+    for (int j = 1; j < 4; ++j)
+      for (int l = 1; l < 4; ++l) {
+        double e = eps(i, j, l);
+        if (e == 0.0) continue;
+        Dense PS, PSg, gPS;
+        dense_mul(Pp, Sig[l], PS);
+        dense_mul(PS, gj[j], PSg);
+        dense_mul(gj[j], PS, gPS);
+        for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) {
+          W_MAG_H[i][j][r][c] += (I / 6.0) * e * PS[r][c];
+          // Tr[PS (-(g M - M g)/4)] = -1/4 (Tr[PS g M] - Tr[g PS M])
+          W_MAG_G[i][r][c] += (I / 6.0) * e * (-0.25) * (PSg[r][c] - gPS[r][c]);
+        }
+      }
+  for (int mu = 0; mu < 4; ++mu) {
+    Dense d; to_dense(GAM_LOW[mu], d);
+    Dense u; to_dense(GAM[mu], u);
+    for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) { W_UV[mu][r][c] = d[r][c] / 16.0; W_WF[mu][r][c] = u[r][c] / 16.0; }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// term structure
+// ---------------------------------------------------------------------------
+enum Kin { KIN_Q, KIN_P, KIN_0, KIN_K };
+enum Proj { PR_F2, PR_L, PR_UV, PR_SEMASS, PR_SEWF };
+
+struct Block {
+  int a, b;              // electron lines a..b
+  bool root, se, has_x;
+  Kin kin;
+  Proj proj;
+  int parent = -1;
+  std::vector<int> children;
+  bool has_pos(int p) const { return p >= a && p <= b + 1; }
+  bool has_line(int l) const { return l >= a && l <= b; }
+  int width() const { return b - a; }
+};
+
+struct Term {
+  int sign;
+  std::vector<Block> blocks;     // blocks[0] = root
+};
+
+static std::vector<Term> build_terms(const Graph &g) {
+  std::vector<Term> out;
+  for (auto &F : forests(g)) {
+    int fsign = (F.size() % 2) ? -1 : 1;
+    std::vector<int> gps = {-1};
+    for (size_t i = 0; i < F.size(); ++i) if (F[i].has_x) gps.push_back(int(i));
+    for (int gp : gps) {
+      // options per element: list of (sign, kin, proj)
+      std::vector<std::vector<std::tuple<int, Kin, Proj>>> opts;
+      for (size_t i = 0; i < F.size(); ++i) {
+        const Sub &s = F[i];
+        if (gp >= 0 && int(i) == gp) opts.push_back({{1, KIN_Q, PR_F2}});
+        else if (gp >= 0 && (s.lines & F[gp].lines) == F[gp].lines && s.lines != F[gp].lines)
+          opts.push_back({{1, KIN_P, PR_L}, {-1, KIN_0, PR_UV}});
+        else if (s.se) opts.push_back({{1, KIN_P, PR_SEMASS}, {1, KIN_K, PR_SEWF}});
+        else opts.push_back({{1, KIN_0, PR_UV}});
+      }
+      std::vector<std::tuple<int, Kin, Proj>> roots;
+      if (gp < 0) roots = {{1, KIN_Q, PR_F2}};
+      else roots = {{1, KIN_P, PR_L}, {-1, KIN_0, PR_UV}};
+      size_t ncomb = 1;
+      for (auto &o : opts) ncomb *= o.size();
+      for (auto &rt : roots)
+        for (size_t c = 0; c < ncomb; ++c) {
+          Term t;
+          t.sign = fsign * std::get<0>(rt);
+          Block r; r.a = 0; r.b = g.n_elec() - 1; r.root = true; r.se = false; r.has_x = true;
+          r.kin = std::get<1>(rt); r.proj = std::get<2>(rt);
+          t.blocks.push_back(r);
+          size_t cc = c;
+          for (size_t i = 0; i < F.size(); ++i) {
+            auto &o = opts[i][cc % opts[i].size()];
+            cc /= opts[i].size();
+            Block b; b.a = F[i].a; b.b = F[i].b; b.root = false; b.se = F[i].se; b.has_x = F[i].has_x;
+            b.kin = std::get<1>(o); b.proj = std::get<2>(o);
+            t.sign *= std::get<0>(o);
+            t.blocks.push_back(b);
+          }
+          // parents
+          for (size_t i = 1; i < t.blocks.size(); ++i) {
+            int best = 0;
+            for (size_t j = 1; j < t.blocks.size(); ++j) {
+              if (j == i) continue;
+              auto &O = t.blocks[j], &B = t.blocks[i];
+              if (O.a <= B.a && B.b <= O.b && O.width() > B.width() && O.width() < t.blocks[best].width()) best = int(j);
+            }
+            t.blocks[i].parent = best;
+            t.blocks[best].children.push_back(int(i));
+          }
+          for (auto &b : t.blocks)
+            std::sort(b.children.begin(), b.children.end(), [&](int x, int y) { return t.blocks[x].a < t.blocks[y].a; });
+          out.push_back(t);
+        }
+    }
+  }
+  return out;
+}
+
+// Item of a block's own Dirac string (increasing position = rightmost first)
+enum ItemKind { IT_VTX_PH, IT_VTX_MU, IT_LINE, IT_SEMASS, IT_INS };
+struct Item {
+  ItemKind kind;
+  int photon = -1;       // IT_VTX_PH
+  int line = -1;         // IT_LINE: line; IT_INS: entering line
+  int child = -1;        // SE child block
+};
+
+struct TermInfo {
+  const Graph *g;
+  Term t;
+  std::vector<int> mb_line, mb_ph;
+  std::vector<std::vector<int>> eta;       // [line][photon] 0/1 (all 3n lines)
+  std::vector<double> alpha, beta, kappa, mass2;
+  std::vector<std::vector<Item>> seq;      // per block
+};
+
+static int min_block_line(const Term &t, int l) {
+  int best = 0;
+  for (size_t i = 0; i < t.blocks.size(); ++i)
+    if (t.blocks[i].has_line(l) && t.blocks[i].width() < t.blocks[best].width()) best = int(i);
+  return best;
+}
+static int min_block_ph(const Graph &g, const Term &t, int a) {
+  auto pp = g.ph_pos(a);
+  int best = 0;
+  for (size_t i = 0; i < t.blocks.size(); ++i)
+    if (t.blocks[i].has_pos(pp.first) && t.blocks[i].has_pos(pp.second) && t.blocks[i].width() < t.blocks[best].width()) best = int(i);
+  return best;
+}
+
+// label a vertex-like child (or a vertex) carries in block bi: photon id or -1 for mu
+static int leg_of_child(const TermInfo &T, int bi, int ci) {
+  const Graph &g = *T.g;
+  const Block &c = T.t.blocks[ci];
+  if (c.has_pos(g.e)) return -1;
+  for (int p = c.a; p <= c.b + 1; ++p) {
+    int a = g.photon_at(p);
+    auto pp = g.ph_pos(a);
+    if (!(c.has_pos(pp.first) && c.has_pos(pp.second))) return T.mb_ph[a] == bi ? a : -1;
+  }
+  fprintf(stderr, "vertex block without leg\n");
+  exit(1);
+}
+
+static TermInfo analyse(const Graph &g, const Term &t) {
+  TermInfo T; T.g = &g; T.t = t;
+  int n = g.n, L = g.n_lines();
+  for (int l = 0; l < g.n_elec(); ++l) T.mb_line.push_back(min_block_line(t, l));
+  for (int a = 0; a < n; ++a) T.mb_ph.push_back(min_block_ph(g, t, a));
+  T.eta.assign(L, std::vector<int>(n, 0));
+  for (int a = 0; a < n; ++a) {
+    auto sp = g.span(a);
+    for (int l = sp.first; l <= sp.second; ++l) if (T.mb_line[l] == T.mb_ph[a]) T.eta[l][a] = 1;
+    T.eta[g.n_elec() + a][a] = 1;
+  }
+  T.alpha.assign(L, 0); T.beta.assign(L, 0); T.kappa.assign(L, 0); T.mass2.assign(L, 0);
+  for (int l = 0; l < g.n_elec(); ++l) {
+    T.mass2[l] = 1.0;
+    Kin k = t.blocks[T.mb_line[l]].kin;
+    double ax = (l >= g.e) ? 1.0 : 0.0;
+    if (k == KIN_Q) { T.alpha[l] = 1.0; T.beta[l] = ax - 0.5; }
+    else if (k == KIN_P) T.alpha[l] = 1.0;
+    else if (k == KIN_K) T.kappa[l] = 1.0;
+  }
+  T.seq.resize(t.blocks.size());
+  for (size_t bi = 0; bi < t.blocks.size(); ++bi) {
+    const Block &B = t.blocks[bi];
+    std::map<int, int> ch;
+    for (int c : B.children) ch[t.blocks[c].a] = c;
+    auto &S = T.seq[bi];
+    int v = B.a;
+    while (v <= B.b + 1) {
+      auto it = ch.find(v);
+      if (it != ch.end()) {
+        const Block &C = t.blocks[it->second];
+        Item I;
+        if (C.se) {
+          if (C.proj == PR_SEMASS) { I.kind = IT_SEMASS; I.child = it->second; }
+          else { I.kind = IT_INS; I.child = it->second; I.line = C.a - 1; }
+        } else {
+          int lab = leg_of_child(T, int(bi), it->second);
+          if (lab < 0) I.kind = IT_VTX_MU; else { I.kind = IT_VTX_PH; I.photon = lab; }
+          I.child = it->second;
+        }
+        S.push_back(I);
+        v = C.b + 1;
+        if (v <= B.b) { Item li; li.kind = IT_LINE; li.line = v; S.push_back(li); }
+        ++v;
+        continue;
+      }
+      Item I;
+      if (v == g.e) I.kind = IT_VTX_MU;
+      else {
+        int a = g.photon_at(v);
+        if (T.mb_ph[a] == int(bi)) { I.kind = IT_VTX_PH; I.photon = a; }
+        else I.kind = IT_VTX_MU;
+      }
+      S.push_back(I);
+      if (v <= B.b) { Item li; li.kind = IT_LINE; li.line = v; S.push_back(li); }
+      ++v;
+    }
+  }
+  return T;
+}
+
+// ---------------------------------------------------------------------------
+// coefficients of one block for one contraction pattern
+// ---------------------------------------------------------------------------
+// Momentum factors of a block: IT_LINE and IT_INS items (indices into seq).
+// Parts of an uncontracted factor: '1' (identity, -1 for an insertion),
+// 'p' (gamma^0, variable A), 'd' (derivative: -gamma^j * C for q, gamma_nu * K
+// for k).  Monomial key = bitmask of 'p' factors (over the block's momentum
+// factor list) and the derivative factor (-1 = none).
+struct MonoKey {
+  uint32_t pmask; int deriv;
+  bool operator<(const MonoKey &o) const { return pmask != o.pmask ? pmask < o.pmask : deriv < o.deriv; }
+};
+
+struct DFS {
+  const std::vector<Item> *seq;
+  Proj proj;
+  bool allow_p, allow_q, allow_k;
+  std::vector<int> slot_of_item;          // momentum-factor index or -1
+  std::vector<int> pair_partner;          // item -> partner item for contracted / photon pairs, -1
+  std::vector<int> pair_alpha;            // chosen alpha per item (filled in DFS)
+  std::map<MonoKey, cd> acc;
+  int nitems;
+
+  void leaf(const Mono &M, int mu, int dj, uint32_t pm, int dv) {
+    cd v = 0;
+    switch (proj) {
+      case PR_F2:
+        if (dv < 0) { if (mu == 0) v = -tr_wm(W_F1, M); else v = tr_wm(W_MAG_G[mu], M); }
+        else { if (mu > 0) v = tr_wm(W_MAG_H[mu][dj], M); }
+        break;
+      case PR_L: if (mu == 0 && dv < 0) v = tr_wm(W_F1, M); break;
+      case PR_UV: if (dv < 0) v = tr_wm(W_UV[mu], M); break;
+      case PR_SEMASS: if (dv < 0) v = tr_wm(W_F1, M); break;
+      case PR_SEWF: if (dv >= 0) v = tr_wm(W_WF[dj], M); break;
+    }
+    if (std::abs(v) > 0) acc[MonoKey{pm, dv}] += v;
+  }
+  // t: current item, M: product of items < t (rightmost first), mu/dj state
+  void go(int t, const Mono &M, int mu, int dj, uint32_t pm, int dv) {
+    if (t == nitems) { leaf(M, mu, dj, pm, dv); return; }
+    const Item &I = (*seq)[t];
+    auto push = [&](const Mono &F, int mu2, int dj2, uint32_t pm2, int dv2) {
+      go(t + 1, mono_mul(F, M), mu2, dj2, pm2, dv2);
+    };
+    if (pair_partner[t] >= 0) {            // contracted gamma slot
+      int p = pair_partner[t];
+      if (p > t) {
+        for (int a = 0; a < 4; ++a) { pair_alpha[t] = a; push(GAM[a], mu, dj, pm, dv); }
+      } else push(GAM_LOW[pair_alpha[p]], mu, dj, pm, dv);
+      return;
+    }
+    switch (I.kind) {
+      case IT_VTX_MU:
+        if (mu >= 0) { fprintf(stderr, "two free indices\n"); exit(1); }
+        for (int m = 0; m < 4; ++m) push(GAM[m], m, dj, pm, dv);
+        return;
+      case IT_SEMASS:
+        push(mono_identity(), mu, dj, pm, dv);
+        return;
+      case IT_LINE:
+      case IT_INS: {
+        int f = slot_of_item[t];
+        Mono one = mono_identity();
+        if (I.kind == IT_INS) for (int r = 0; r < 4; ++r) one.val[r] = -1.0;
+        push(one, mu, dj, pm, dv);
+        if (allow_p) push(GAM[0], mu, dj, pm | (1u << f), dv);
+        if (dv < 0 && allow_q)
+          for (int j = 1; j < 4; ++j) { Mono m = GAM[j]; for (int r = 0; r < 4; ++r) m.val[r] = -m.val[r]; push(m, mu, j, pm, f); }
+        if (dv < 0 && allow_k)
+          for (int nu = 0; nu < 4; ++nu) push(GAM_LOW[nu], mu, nu, pm, f);
+        return;
+      }
+      default: break;
+    }
+    fprintf(stderr, "bad item\n");
+    exit(1);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// code emission
+// ---------------------------------------------------------------------------
+static std::string dstr(double x) {
+  char b[64];
+  snprintf(b, sizeof b, "%.17g", x);
+  std::string s = b;
+  if (s.find('.') == std::string::npos && s.find('e') == std::string::npos) s += ".0";
+  return s;
+}
+
+struct Emitter {
+  std::ostringstream os;
+  int tmp = 0;
+  std::string fresh(const char *p) { return std::string(p) + std::to_string(tmp++); }
+};
+
+// Emit a sum of z's (as R expression); returns "" if empty
+static std::string zsum(const std::vector<int> &ls) {
+  if (ls.empty()) return "";
+  std::string s;
+  for (size_t i = 0; i < ls.size(); ++i) s += (i ? " + z[" : "z[") + std::to_string(ls[i]) + "]";
+  return s;
+}
+
+struct GenStats { long terms = 0, monos = 0; };
+
+// Emits code computing one term's value into variable `out` (declared here).
+static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, GenStats &st) {
+  const Graph &g = *T.g;
+  int n = g.n, L = g.n_lines();
+  auto &os = E.os;
+  std::string P = E.fresh("t");
+  // Lambda entries
+  std::vector<std::vector<std::string>> lam(n, std::vector<std::string>(n));
+  for (int a = 0; a < n; ++a)
+    for (int b = a; b < n; ++b) {
+      std::vector<int> ls;
+      for (int l = 0; l < L; ++l) if (T.eta[l][a] && T.eta[l][b]) ls.push_back(l);
+      if (ls.empty()) { lam[a][b] = lam[b][a] = ""; continue; }
+      std::string v = P + "_L" + std::to_string(a) + std::to_string(b);
+      os << "    const R " << v << " = " << zsum(ls) << ";\n";
+      lam[a][b] = lam[b][a] = v;
+    }
+  // determinant and adjugate (cofactors), n <= 3 written out
+  auto L_ = [&](int a, int b) -> std::string { return lam[a][b].empty() ? "R(0.0)" : lam[a][b]; };
+  std::vector<std::vector<std::string>> adj(n, std::vector<std::string>(n));
+  std::string U = P + "_U";
+  if (n == 1) {
+    os << "    const R " << U << " = " << L_(0, 0) << ";\n";
+    adj[0][0] = "R(1.0)";
+  } else if (n == 2) {
+    os << "    const R " << U << " = " << L_(0, 0) << " * " << L_(1, 1) << " - " << L_(0, 1) << " * " << L_(0, 1) << ";\n";
+    adj[0][0] = L_(1, 1); adj[1][1] = L_(0, 0);
+    adj[0][1] = adj[1][0] = lam[0][1].empty() ? "R(0.0)" : "(-" + L_(0, 1) + ")";
+  } else if (n == 3) {
+    auto cof = [&](int r, int c) {
+      int r1 = (r + 1) % 3, r2 = (r + 2) % 3, c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+      return "(" + L_(r1, c1) + " * " + L_(r2, c2) + " - " + L_(r1, c2) + " * " + L_(r2, c1) + ")";
+    };
+    for (int r = 0; r < 3; ++r) for (int c = r; c < 3; ++c) {
+      std::string v = P + "_A" + std::to_string(r) + std::to_string(c);
+      os << "    const R " << v << " = " << cof(c, r) << ";\n";
+      adj[r][c] = adj[c][r] = v;
+    }
+    os << "    const R " << U << " = " << L_(0, 0) << " * " << adj[0][0] << " + " << L_(0, 1) << " * " << adj[1][0]
+       << " + " << L_(0, 2) << " * " << adj[2][0] << ";\n";
+  } else {
+    fprintf(stderr, "loop order %d not supported by the emitter\n", n);
+    exit(1);
+  }
+  os << "    const R " << P << "_iU = R(1.0) / " << U << ";\n";
+  // J vectors and Q coefficients for every line with a non-zero coefficient
+  auto emitJ = [&](const std::vector<double> &coef, const char *tag) -> std::vector<std::string> {
+    std::vector<std::string> J(n);
+    for (int a = 0; a < n; ++a) {
+      std::string s;
+      for (int l = 0; l < L; ++l)
+        if (T.eta[l][a] && coef[l] != 0.0) {
+          std::string term = (coef[l] == 1.0 ? "" : dstr(coef[l]) + " * ") + "z[" + std::to_string(l) + "]";
+          s += s.empty() ? term : " + " + term;
+        }
+      if (s.empty()) { J[a] = ""; continue; }
+      J[a] = P + "_J" + tag + std::to_string(a);
+      os << "    const R " << J[a] << " = " << s << ";\n";
+    }
+    return J;
+  };
+  // adj * J
+  auto emitAJ = [&](const std::vector<std::string> &J, const char *tag) -> std::vector<std::string> {
+    std::vector<std::string> X(n);
+    for (int a = 0; a < n; ++a) {
+      std::string s;
+      for (int b = 0; b < n; ++b) if (!J[b].empty() && !(adj[a][b] == "R(0.0)")) s += (s.empty() ? "" : " + ") + adj[a][b] + " * " + J[b];
+      if (s.empty()) continue;
+      X[a] = P + "_X" + tag + std::to_string(a);
+      os << "    const R " << X[a] << " = " << s << ";\n";
+    }
+    return X;
+  };
+  auto coefQ = [&](const std::vector<double> &coef, const std::vector<std::string> &X, int l, const char *tag) -> std::string {
+    // Q coefficient of line l: coef_l - (eta_l . adj . J) / U
+    std::string s;
+    for (int a = 0; a < n; ++a) if (T.eta[l][a] && !X[a].empty()) s += (s.empty() ? "" : " + ") + X[a];
+    std::string v = P + "_" + tag + std::to_string(l);
+    if (s.empty()) { os << "    const R " << v << " = R(" << dstr(coef[l]) << ");\n"; return v; }
+    os << "    const R " << v << " = R(" << dstr(coef[l]) << ") - (" << s << ") * " << P << "_iU;\n";
+    return v;
+  };
+  auto Jp = emitJ(T.alpha, "p"), Jq = emitJ(T.beta, "q"), Jk = emitJ(T.kappa, "k");
+  auto Xp = emitAJ(Jp, "p"), Xq = emitAJ(Jq, "q"), Xk = emitAJ(Jk, "k");
+  bool anyp = false, anyq = false, anyk = false;
+  for (int l = 0; l < L; ++l) { anyp |= T.alpha[l] != 0; anyq |= T.beta[l] != 0; anyk |= T.kappa[l] != 0; }
+  std::vector<std::string> A(L), C(L), K(L);
+  // V = sum_e z - sum_l z_l A_l^2
+  std::string V = P + "_V";
+  {
+    std::string s;
+    for (int l = 0; l < g.n_elec(); ++l) s += (s.empty() ? "" : " + ") + std::string("z[") + std::to_string(l) + "]";
+    os << "    R " << V << " = " << s << ";\n";
+    if (anyp)
+      for (int l = 0; l < L; ++l) {
+        bool need = T.alpha[l] != 0.0;
+        for (int a = 0; a < n; ++a) if (T.eta[l][a] && !Xp[a].empty()) need = true;
+        if (!need) continue;
+        A[l] = coefQ(T.alpha, Xp, l, "Ap");
+        os << "    " << V << " = " << V << " - z[" << l << "] * " << A[l] << " * " << A[l] << ";\n";
+      }
+  }
+  if (anyq) for (int l = 0; l < g.n_elec(); ++l) {
+    bool need = T.beta[l] != 0.0;
+    for (int a = 0; a < n; ++a) if (T.eta[l][a] && !Xq[a].empty()) need = true;
+    if (need) C[l] = coefQ(T.beta, Xq, l, "Cq");
+  }
+  if (anyk) for (int l = 0; l < g.n_elec(); ++l) {
+    bool need = T.kappa[l] != 0.0;
+    for (int a = 0; a < n; ++a) if (T.eta[l][a] && !Xk[a].empty()) need = true;
+    if (need) K[l] = coefQ(T.kappa, Xk, l, "Kk");
+  }
+  // B_ij on demand
+  std::map<std::pair<int, int>, std::string> Bc;
+  auto Bij = [&](int i, int j) -> std::string {
+    if (i > j) std::swap(i, j);
+    auto key = std::make_pair(i, j);
+    auto it = Bc.find(key);
+    if (it != Bc.end()) return it->second;
+    std::string s;
+    for (int a = 0; a < n; ++a) for (int b = 0; b < n; ++b)
+      if (T.eta[i][a] && T.eta[j][b] && adj[a][b] != "R(0.0)") s += (s.empty() ? "" : " + ") + adj[a][b];
+    std::string v = s.empty() ? "" : P + "_B" + std::to_string(i) + "_" + std::to_string(j);
+    if (!s.empty()) os << "    const R " << v << " = " << s << ";\n";
+    Bc[key] = v;
+    return v;
+  };
+  // block values: recursive, returns vector of variable names per k
+  std::function<std::vector<std::string>(int)> block_val = [&](int bi) -> std::vector<std::string> {
+    const Block &B = T.t.blocks[bi];
+    const auto &seq = T.seq[bi];
+    std::vector<std::vector<std::string>> childv;
+    for (int c : B.children) childv.push_back(block_val(c));
+    // momentum factors
+    std::vector<int> mom_items;
+    std::vector<int> mom_line;   // line whose eta/A/C/K the factor uses
+    for (size_t t = 0; t < seq.size(); ++t)
+      if (seq[t].kind == IT_LINE || seq[t].kind == IT_INS) { mom_items.push_back(int(t)); mom_line.push_back(seq[t].line); }
+    std::vector<std::pair<int, int>> ph_pairs;
+    {
+      std::map<int, std::vector<int>> byph;
+      for (size_t t = 0; t < seq.size(); ++t) if (seq[t].kind == IT_VTX_PH) byph[seq[t].photon].push_back(int(t));
+      for (auto &kv : byph) {
+        if (kv.second.size() != 2) { fprintf(stderr, "unpaired photon\n"); exit(1); }
+        ph_pairs.push_back({kv.second[0], kv.second[1]});
+      }
+    }
+    int m = int(mom_items.size());
+    // enumerate pairings of momentum factors
+    std::vector<std::vector<std::pair<int, int>>> pats;
+    std::function<void(std::vector<int>, std::vector<std::pair<int, int>>)> rec =
+        [&](std::vector<int> rest, std::vector<std::pair<int, int>> cur) {
+          if (rest.size() < 2) { pats.push_back(cur); return; }
+          int f = rest[0];
+          std::vector<int> r1(rest.begin() + 1, rest.end());
+          rec(r1, cur);
+          for (size_t i = 0; i < r1.size(); ++i) {
+            std::vector<int> r2;
+            for (size_t j = 0; j < r1.size(); ++j) if (j != i) r2.push_back(r1[j]);
+            auto c2 = cur; c2.push_back({f, r1[i]});
+            rec(r2, c2);
+          }
+        };
+    std::vector<int> all(m);
+    for (int i = 0; i < m; ++i) all[i] = i;
+    rec(all, {});
+    std::map<int, std::string> ownk;    // k -> accumulated expression variable
+    for (auto &pat : pats) {
+      // B product
+      std::string bprod;
+      bool zero = false;
+      for (auto &pr : pat) {
+        std::string b = Bij(mom_line[pr.first], mom_line[pr.second]);
+        if (b.empty()) { zero = true; break; }
+        bprod += (bprod.empty() ? "" : " * ") + b;
+      }
+      if (zero) continue;
+      DFS D;
+      D.seq = &seq; D.proj = B.proj; D.nitems = int(seq.size());
+      D.allow_p = (B.kin == KIN_Q || B.kin == KIN_P);
+      D.allow_q = (B.proj == PR_F2);
+      D.allow_k = (B.proj == PR_SEWF);
+      D.slot_of_item.assign(seq.size(), -1);
+      for (int i = 0; i < m; ++i) D.slot_of_item[mom_items[i]] = i;
+      D.pair_partner.assign(seq.size(), -1);
+      D.pair_alpha.assign(seq.size(), 0);
+      for (auto &pp : ph_pairs) { D.pair_partner[pp.first] = pp.second; D.pair_partner[pp.second] = pp.first; }
+      for (auto &pr : pat) { int a = mom_items[pr.first], b = mom_items[pr.second]; D.pair_partner[a] = b; D.pair_partner[b] = a; }
+      D.go(0, mono_identity(), -1, -1, 0u, -1);
+      std::string poly;
+      for (auto &kv : D.acc) {
+        cd c = kv.second;
+        if (std::abs(c.imag()) > 1e-9 * (1 + std::abs(c.real()))) { fprintf(stderr, "complex coefficient %g %g\n", c.real(), c.imag()); exit(1); }
+        double cr = c.real();
+        if (std::abs(cr) < 1e-12) continue;
+        std::string mono;
+        for (int f = 0; f < m; ++f) if (kv.first.pmask >> f & 1) {
+          const std::string &v = A[mom_line[f]];
+          if (v.empty()) { mono = "ZERO"; break; }
+          mono += " * " + v;
+        }
+        if (mono == "ZERO") continue;
+        if (kv.first.deriv >= 0) {
+          int f = kv.first.deriv;
+          const std::string &v = (B.proj == PR_F2) ? C[mom_line[f]] : K[mom_line[f]];
+          if (v.empty()) continue;
+          mono += " * " + v;
+        }
+        poly += (poly.empty() ? "R(" : " + R(") + dstr(cr) + ")" + mono;
+        ++st.monos;
+      }
+      if (poly.empty()) continue;
+      int k = int(pat.size());
+      std::string var = P + "_b" + std::to_string(bi) + "k" + std::to_string(k);
+      std::string contrib = bprod.empty() ? "(" + poly + ")" : bprod + " * (" + poly + ")";
+      if (!ownk.count(k)) { os << "    R " << var << " = " << contrib << ";\n"; ownk[k] = var; }
+      else os << "    " << var << " = " << var << " + " << contrib << ";\n";
+    }
+    int kmax = ownk.empty() ? 0 : ownk.rbegin()->first;
+    std::vector<std::string> vals(kmax + 1);
+    for (int k = 0; k <= kmax; ++k) vals[k] = ownk.count(k) ? ownk[k] : "";
+    for (auto &cv : childv) {
+      std::vector<std::string> nv(vals.size() + cv.size() - 1);
+      for (size_t i = 0; i < vals.size(); ++i) for (size_t j = 0; j < cv.size(); ++j) {
+        if (vals[i].empty() || cv[j].empty()) continue;
+        std::string v = P + "_c" + std::to_string(bi) + "_" + std::to_string(E.tmp++);
+        os << "    const R " << v << " = " << vals[i] << " * " << cv[j] << ";\n";
+        nv[i + j] = nv[i + j].empty() ? v : "(" + nv[i + j] + " + " + v + ")";
+      }
+      vals = nv;
+    }
+    return vals;
+  };
+  auto vals = block_val(0);
+  // combine: (-1)^n 4^-n sum_k (-1)^k Gamma(n-k) U^-2 V^(k-n) (2U)^-k val_k
+  os << "    const R " << P << "_iV = R(1.0) / " << V << ";\n";
+  std::string acc;
+  for (int k = 0; k < n && k < int(vals.size()); ++k) {
+    if (vals[k].empty()) continue;
+    double c = ((n + k) % 2 ? -1.0 : 1.0) * std::tgamma(double(n - k)) * std::pow(4.0, -n) * std::pow(2.0, -k);
+    std::string f = "R(" + dstr(c) + ")";
+    for (int i = 0; i < n - k; ++i) f += " * " + P + "_iV";
+    for (int i = 0; i < 2 + k; ++i) f += " * " + P + "_iU";
+    acc += (acc.empty() ? "" : " + ") + f + " * " + vals[k];
+  }
+  if (acc.empty()) acc = "R(0.0)";
+  os << "    const R " << out << " = R(" << T.t.sign << ".0) * (" << acc << ");\n";
+  ++st.terms;
+}
+
+int main(int argc, char **argv) {
+  if (argc < 3) { fprintf(stderr, "usage: qed_gen out.cu n1 [n2 ...]\n"); return 2; }
+  init_gammas();
+  init_projectors();
+  std::ofstream f(argv[1]);
+  f << "// Generated by qed_gen from the forest-like subtraction formula. Do not edit.\n";
+  f << "// One device function per vertex graph: the subtracted Feynman-parametric\n";
+  f << "// integrand, homogeneous of degree -3n in z; absum receives the sum of the\n";
+  f << "// absolute values of the forest terms (cancellation measure).\n";
+  f << "#pragma once\n\n";
+  std::vector<std::string> reg;
+  GenStats st;
+  for (int ai = 2; ai < argc; ++ai) {
+    int n = atoi(argv[ai]);
+    auto gs = enumerate_graphs(n);
+    for (size_t gi = 0; gi < gs.size(); ++gi) {
+      const Graph &g = gs[gi];
+      auto terms = build_terms(g);
+      Emitter E;
+      std::vector<std::string> outs;
+      for (auto &t : terms) {
+        TermInfo T = analyse(g, t);
+        std::string o = "term" + std::to_string(outs.size());
+        emit_term(E, T, o, st);
+        outs.push_back(o);
+      }
+      f << "// " << g.name() << ": " << terms.size() << " forest terms\n";
+      f << "template <class R>\n__device__ __forceinline__ R qed_f_" << g.name() << "(const R* __restrict__ z, double& absum) {\n";
+      f << E.os.str();
+      f << "    absum = 0.0;\n";
+      for (auto &o : outs) f << "    absum += fabs(to_double(" << o << "));\n";
+      f << "    return ";
+      for (size_t i = 0; i < outs.size(); ++i) f << (i ? " + " : "") << outs[i];
+      f << ";\n}\n\n";
+      reg.push_back(g.name());
+    }
+  }
+  // dispatch table by registry index
+  f << "#define QED_N_GENERATED " << reg.size() << "\n";
+  f << "static const char* const qed_generated_names[] = {";
+  for (size_t i = 0; i < reg.size(); ++i) f << (i ? ", " : "") << "\"" << reg[i] << "\"";
+  f << "};\n\n";
+  f << "template <class R>\n__device__ __forceinline__ R qed_integrand(int fid, const R* __restrict__ z, double& absum) {\n";
+  f << "    switch (fid) {\n";
+  for (size_t i = 0; i < reg.size(); ++i) f << "    case " << i << ": return qed_f_" << reg[i] << "<R>(z, absum);\n";
+  f << "    default: absum = 0.0; return R(0.0);\n    }\n}\n";
+  fprintf(stderr, "qed_gen: %zu graphs, %ld terms, %ld monomials\n", reg.size(), st.terms, st.monos);
+  return 0;
+}
