@@ -427,6 +427,16 @@ static std::string dstr(double x) {
   return s;
 }
 
+// Dirac coefficients are rationals whose denominators divide 2^12 * 3;
+// summing them in floating point leaves last-bit noise, removed here.
+static double snap(double c) {
+  const double den = 4096.0 * 3.0;
+  double r = std::round(c * den);
+  if (std::abs(c * den - r) < 1e-6) return r / den;
+  fprintf(stderr, "coefficient %.17g is not a small rational\n", c);
+  exit(1);
+}
+
 struct Emitter {
   std::ostringstream os;
   int tmp = 0;
@@ -636,8 +646,8 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
       for (auto &kv : D.acc) {
         cd c = kv.second;
         if (std::abs(c.imag()) > 1e-9 * (1 + std::abs(c.real()))) { fprintf(stderr, "complex coefficient %g %g\n", c.real(), c.imag()); exit(1); }
-        double cr = c.real();
-        if (std::abs(cr) < 1e-12) continue;
+        double cr = snap(c.real());
+        if (cr == 0.0) continue;
         std::string mono;
         for (int f = 0; f < m; ++f) if (kv.first.pmask >> f & 1) {
           const std::string &v = A[mom_line[f]];
