@@ -1,0 +1,144 @@
+/*
+ * qedmc -- C ABI of the B300 Monte Carlo integrator for the lepton-loop-free
+ * QED vertex graphs of arXiv:1905.08007 (Volkov, 5-loop electron AMM).
+ *
+ * The paper states the problem as: each vertex graph G of order n contributes
+ * one Feynman-parametric integral a_G of a pointwise-subtracted integrand, and
+ * A_1^(2n) = sum_G a_G (Sec. 2, items 3-4); a_G is estimated by nonadaptive
+ * Monte Carlo with the per-graph density of Eq. (1) (Sec. 2) on GPUs (Sec. 3).
+ * This header exposes exactly that: load a graph (with its generated
+ * integrand and its Deg-based density), then integrate it.
+ *
+ * Conventions shared by every call:
+ *  - Return value: 0 = QED_OK, negative = error code below.  No call throws.
+ *    qed_last_error() returns a thread-local message for the last failure.
+ *  - Graph: n photons; photon a joins photon vertices pairs[2a] < pairs[2a+1]
+ *    (vertices 0..2n-1 along the electron flow); the external photon vertex
+ *    sits after the first e photon vertices.  Lines: electron lines 0..2n-1
+ *    along the flow, then photons 2n..3n-1.
+ *  - Random numbers: Philox4x32-10 (Sec. 3, Calc 2), counter = (sample lo32,
+ *    sample hi32, graph stream id, block), key = (seed lo32, seed hi32).
+ *    Sample s uses draws 0..N-2 for the Hepp-sector walk and N-1..2N-3 for
+ *    the radial variables, two draws per Philox block.  Results depend only
+ *    on (seed, stream id, sample range, launch shape).
+ *  - All pointers are owned by the caller unless stated otherwise; the
+ *    library copies what it keeps.  Device pointers must be on the context's
+ *    device.  Calls on one context are not thread-safe.
+ */
+#ifndef QEDMC_H
+#define QEDMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QED_OK 0
+#define QED_EINVAL (-1)            /* bad argument or unsupported graph */
+#define QED_ENOMEM (-2)            /* device or host allocation failed */
+#define QED_ECUDA (-3)             /* a CUDA runtime call failed */
+#define QED_ETIMEOUT (-4)          /* a bounded device wait gave up */
+#define QED_EUNSTABLE_LIMIT (-5)   /* more unstable points than allowed */
+#define QED_ENOTFOUND (-6)         /* no generated integrand for this graph */
+
+#define QED_MAX_LOOPS 5
+
+typedef struct qed_ctx qed_ctx;
+typedef struct qed_diag qed_diag;
+
+/* A vertex graph without lepton loops (Sec. 3: "diagrams without lepton
+ * loops"; mirror images are distinct graphs here).  stream_id is the third
+ * Philox counter word used for this graph's samples. */
+typedef struct {
+  int n;                          /* loops = internal photons, 1..QED_MAX_LOOPS */
+  int pairs[2 * QED_MAX_LOOPS];   /* photon a: vertices pairs[2a] < pairs[2a+1] */
+  int e;                          /* external vertex after e photon vertices */
+  uint32_t stream_id;
+} qed_graph;
+
+/* Density of Eq. (1).  If deg != NULL it holds Deg(s) for every subset s of
+ * the N = 3n lines as a bitmask-indexed array of 2^N doubles (entries 0 and
+ * 2^N-1 unused); all used entries must be > 0 (else QED_EINVAL).  If deg is
+ * NULL the library builds Deg(s) = -omega(I-closure(s)) when positive, else
+ * c_div, floored at d_min (Sec. 2: Deg from omega of I-closures, sometimes
+ * fractional and below 1). */
+typedef struct {
+  const double *deg;
+  double c_div;                   /* default 0.5 when <= 0 */
+  double d_min;                   /* default 0.05 when <= 0 */
+} qed_pdf;
+
+/* Per-graph Monte Carlo result in units of (alpha/pi)^n (Sec. 3). */
+typedef struct {
+  double value;                   /* mean of f/p */
+  double variance;                /* variance of the mean */
+  double sum_w[2];                /* sum of w = f/p as a double-double (hi, lo) */
+  double sum_w2[2];               /* sum of w^2 as a double-double */
+  uint64_t n;                     /* samples */
+  uint64_t n_flagged;             /* points re-evaluated in double-double */
+  uint64_t n_unstable;            /* points unstable in double-double: w := 0 */
+  double seconds;                 /* device time of the call */
+} qed_result;
+
+/* ---- context ------------------------------------------------------------ */
+/* Create a context on CUDA device `device`.  flags: reserved, pass 0.  The
+ * context owns every device buffer it allocates. */
+int qed_ctx_create(int device, uint64_t flags, qed_ctx **out);
+int qed_ctx_destroy(qed_ctx *ctx);
+/* Launch subsequent work on this cudaStream_t (0 = legacy default stream). */
+int qed_ctx_set_stream(qed_ctx *ctx, uintptr_t stream);
+/* Launch shape of the integration kernels: threads per block (multiple of 32,
+ * <= 1024) and blocks (0 = 4 x the SM count).  Results depend on it through
+ * the summation order only. */
+int qed_ctx_set_launch(qed_ctx *ctx, int threads_per_block, int blocks);
+/* Relative rounding-error threshold above which a point is re-evaluated in
+ * double-double (Sec. 3: arithmetics of different precisions).  Default 1e-9. */
+int qed_ctx_set_threshold(qed_ctx *ctx, double rel_err);
+const char *qed_last_error(void);
+
+/* ---- graphs ------------------------------------------------------------- */
+/* Enumerate the graphs of order n (Sec. 3, Table 1 counts): all of them
+ * (reduced = 0) or one per mirror pair (reduced = 1, the lexicographically
+ * smaller key).  Writes min(count, cap) graphs to out (may be NULL when
+ * cap = 0) and the total to *count.  stream_id = index in the list. */
+int qed_enumerate(int n, int reduced, qed_graph *out, int cap, int *count);
+/* Gauge-invariant class (k, m, n) of Table 1: photons spanning X, photons on
+ * the larger and on the smaller side of X. */
+int qed_gauge_class(const qed_graph *g, int kmn[3]);
+
+/* Load a graph: validate it (lepton-loop free, one-particle irreducible, no
+ * self-energy on an external leg), select its generated integrand, build and
+ * upload the Eq. (1) tables.  QED_ENOTFOUND if the library holds no generated
+ * integrand for this graph. */
+int qed_diagram_load(qed_ctx *ctx, const qed_graph *g, const qed_pdf *pdf, qed_diag **out);
+int qed_diagram_free(qed_diag *d);
+/* N = 3n lines, generated integrand id, log of the Eq. (1) normaliser F(E). */
+int qed_diagram_info(const qed_diag *d, int *n_lines, int *integrand_id, double *log_norm);
+
+/* ---- integration (Sec. 2 nonadaptive MC, Sec. 3) ------------------------- */
+/* Estimate a_G from samples [0, n_samples). */
+int qed_integrate(qed_diag *d, uint64_t n_samples, uint64_t seed, qed_result *out);
+/* Same over samples [begin, begin + n): disjoint ranges give independent
+ * replicas whose moments merge exactly (resume, multi-process). */
+int qed_integrate_range(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed, qed_result *out);
+
+/* Parity mode: for samples [begin, begin + n) write, into caller-owned DEVICE
+ * buffers, the point z (n x N doubles, row-major, largest component 1), the
+ * integrand f (FP64 path), log p(z) of Eq. (1) and a flag byte (bit 0: the
+ * rounding-error estimate exceeded the threshold; bit 1: non-finite). */
+int qed_dump_points(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed,
+                    double *z_dev, double *f_dev, double *logp_dev, uint8_t *flag_dev);
+/* Evaluate the integrand at caller-supplied DEVICE points z (n x N) in FP64
+ * (prec = 0) or double-double (prec = 1, result rounded to double). */
+int qed_eval_points(qed_diag *d, const double *z_dev, uint64_t n, int prec, double *f_dev);
+
+/* Merge replica results (Chan et al. pairwise update of the moments in
+ * double-double, fixed order): out = a (+) b. */
+int qed_result_merge(const qed_result *a, const qed_result *b, qed_result *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QEDMC_H */
