@@ -1,0 +1,118 @@
+"""Build the native library in-tree: run the integrand generator, then nvcc.
+
+    python -m paper_1905_08007_b300.build [--orders 1 2 3] [--jobs 8]
+
+Steps:
+1. compile ``csrc/qed_gen.cpp`` with g++ and run it for the requested loop
+   orders; it writes ``csrc/_gen/g_<id>.cuh`` (one device function per vertex
+   graph, the forest-subtracted integrand) and ``csrc/_gen/qed_registry.h``;
+2. compile one translation unit per graph (the kernels instantiated for that
+   integrand) plus ``csrc/qedmc.cu`` (host side, C ABI) for sm_103a, in
+   parallel, and link them into ``libqedmc.so`` next to this file.
+"""
+from __future__ import annotations
+
+import argparse
+import re
+from concurrent.futures import ThreadPoolExecutor
+import hashlib
+import os
+import shutil
+import subprocess
+import sys
+from pathlib import Path
+
+PKG = Path(__file__).resolve().parent
+CSRC = PKG / "csrc"
+GEN = CSRC / "_gen"
+ROOT = PKG.parent
+INCLUDE = ROOT / "include"
+BUILD = ROOT / "_build"
+LIB = PKG / "libqedmc.so"
+DEFAULT_ORDERS = (1, 2, 3)
+ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+
+
+def _run(cmd, **kw):
+    print("+", " ".join(str(c) for c in cmd), flush=True)
+    subprocess.run([str(c) for c in cmd], check=True, **kw)
+
+
+def _nvcc():
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", shutil.which("nvcc")):
+        if c and Path(c).exists():
+            return c
+    raise RuntimeError("nvcc not found")
+
+
+def _digest(paths, extra=""):
+    h = hashlib.sha256(extra.encode())
+    for p in paths:
+        h.update(Path(p).read_bytes())
+    return h.hexdigest()
+
+
+def build(orders=DEFAULT_ORDERS, force=False, verbose_ptxas=False, jobs=None):
+    orders = tuple(int(o) for o in orders)
+    BUILD.mkdir(exist_ok=True)
+    GEN.mkdir(exist_ok=True)
+    gen_src = [CSRC / "qed_gen.cpp", CSRC / "qed_graph.hpp"]
+    lib_src = [CSRC / "qedmc.cu", CSRC / "qed_kernels.cuh", CSRC / "qed_dd.cuh",
+               CSRC / "qed_graph.hpp", INCLUDE / "qedmc.h"]
+    stamp = BUILD / "libqedmc.stamp"
+    key = _digest(gen_src + lib_src, extra=repr(orders) + ARCH + repr(verbose_ptxas))
+    if not force and LIB.exists() and stamp.exists() and stamp.read_text() == key:
+        return LIB
+    gen_bin = BUILD / "qed_gen"
+    _run(["g++", "-O2", "-std=c++17", "-o", gen_bin, CSRC / "qed_gen.cpp"])
+    for old in GEN.glob("*"):
+        old.unlink()
+    _run([gen_bin, GEN] + list(orders))
+    reg = (GEN / "qed_registry.h").read_text()
+    ids = re.findall(r"X\((\d+), (\d+)\)", reg.split("QED_GENERATED_LIST(X)")[1].splitlines()[0])
+    objdir = BUILD / "obj"
+    objdir.mkdir(exist_ok=True)
+    for old in objdir.glob("*.o"):
+        old.unlink()
+    base = [_nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+            "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC, "-I", GEN]
+    if verbose_ptxas:
+        base.append("-Xptxas=-v")
+    units = []
+    for gid, lines in ids:
+        tu = GEN / f"k_{gid}.cu"
+        tu.write_text(f'#include "qed_kernels.cuh"\n#include "g_{gid}.cuh"\nQED_DEFINE_KSET({gid}, {lines})\n')
+        units.append((tu, objdir / f"k_{gid}.o"))
+    units.append((CSRC / "qedmc.cu", objdir / "qedmc.o"))
+
+    def compile_one(u):
+        src, obj = u
+        cmd = base + ["-c", "-o", obj, src]
+        r = subprocess.run([str(c) for c in cmd], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
+        return src, r.stderr
+
+    jobs = jobs or max(1, os.cpu_count() or 1)
+    print(f"+ nvcc {len(units)} translation units, {jobs} jobs", flush=True)
+    with ThreadPoolExecutor(max_workers=jobs) as ex:
+        for src, err in ex.map(compile_one, units):
+            if verbose_ptxas and err:
+                print(f"== {src.name}\n{err}")
+    _run([_nvcc(), ARCH, "-shared", "-o", LIB] + [o for _, o in units] + ["-lcudart"])
+    stamp.write_text(key)
+    return LIB
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--orders", nargs="*", type=int, default=list(DEFAULT_ORDERS))
+    ap.add_argument("--force", action="store_true")
+    ap.add_argument("--ptxas-v", action="store_true")
+    ap.add_argument("--jobs", type=int, default=None)
+    a = ap.parse_args(argv)
+    print(build(a.orders, force=a.force, verbose_ptxas=a.ptxas_v, jobs=a.jobs))
+
+
+if __name__ == "__main__":
+    sys.exit(main())

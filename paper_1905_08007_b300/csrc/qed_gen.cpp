@@ -505,7 +505,7 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
       std::string s;
       for (int l = 0; l < L; ++l)
         if (T.eta[l][a] && coef[l] != 0.0) {
-          std::string term = (coef[l] == 1.0 ? "" : dstr(coef[l]) + " * ") + "z[" + std::to_string(l) + "]";
+          std::string term = (coef[l] == 1.0 ? "" : "R(" + dstr(coef[l]) + ") * ") + "z[" + std::to_string(l) + "]";
           s += s.empty() ? term : " + " + term;
         }
       if (s.empty()) { J[a] = ""; continue; }
@@ -704,16 +704,17 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
 }
 
 int main(int argc, char **argv) {
-  if (argc < 3) { fprintf(stderr, "usage: qed_gen out.cu n1 [n2 ...]\n"); return 2; }
+  if (argc < 3) { fprintf(stderr, "usage: qed_gen out_dir n1 [n2 ...]\n"); return 2; }
   init_gammas();
   init_projectors();
-  std::ofstream f(argv[1]);
-  f << "// Generated by qed_gen from the forest-like subtraction formula. Do not edit.\n";
-  f << "// One device function per vertex graph: the subtracted Feynman-parametric\n";
-  f << "// integrand, homogeneous of degree -3n in z; absum receives the sum of the\n";
-  f << "// absolute values of the forest terms (cancellation measure).\n";
-  f << "#pragma once\n\n";
+  const std::string dir = argv[1];
+  const char *banner =
+      "// Generated by qed_gen from the forest-like subtraction formula. Do not edit.\n"
+      "// Subtracted Feynman-parametric integrand of one vertex graph, homogeneous\n"
+      "// of degree -3n in z; absum receives the sum of the absolute values of the\n"
+      "// forest terms (the cancellation measure used by the rounding-error flag).\n";
   std::vector<std::string> reg;
+  std::vector<int> reg_lines;
   GenStats st;
   for (int ai = 2; ai < argc; ++ai) {
     int n = atoi(argv[ai]);
@@ -729,6 +730,9 @@ int main(int argc, char **argv) {
         emit_term(E, T, o, st);
         outs.push_back(o);
       }
+      const int id = int(reg.size());
+      std::ofstream f(dir + "/g_" + std::to_string(id) + ".cuh");
+      f << banner << "#pragma once\n\n";
       f << "// " << g.name() << ": " << terms.size() << " forest terms\n";
       f << "template <class R>\n__device__ __forceinline__ R qed_f_" << g.name() << "(const R* __restrict__ z, double& absum) {\n";
       f << E.os.str();
@@ -737,18 +741,21 @@ int main(int argc, char **argv) {
       f << "    return ";
       for (size_t i = 0; i < outs.size(); ++i) f << (i ? " + " : "") << outs[i];
       f << ";\n}\n\n";
+      f << "template <int FID> struct qed_gen_f;\n";
+      f << "template <> struct qed_gen_f<" << id << "> { template <class R> __device__ static __forceinline__ R eval(const R* __restrict__ z, double& absum) { return qed_f_" << g.name() << "<R>(z, absum); } };\n";
       reg.push_back(g.name());
+      reg_lines.push_back(g.n_lines());
     }
   }
-  // dispatch table by registry index
+  std::ofstream f(dir + "/qed_registry.h");
+  f << "// Generated by qed_gen. Registry of the generated integrands.\n#pragma once\n";
   f << "#define QED_N_GENERATED " << reg.size() << "\n";
+  f << "// X(id, lines)\n#define QED_GENERATED_LIST(X)";
+  for (size_t i = 0; i < reg.size(); ++i) f << " X(" << i << ", " << reg_lines[i] << ")";
+  f << "\n";
   f << "static const char* const qed_generated_names[] = {";
   for (size_t i = 0; i < reg.size(); ++i) f << (i ? ", " : "") << "\"" << reg[i] << "\"";
-  f << "};\n\n";
-  f << "template <class R>\n__device__ __forceinline__ R qed_integrand(int fid, const R* __restrict__ z, double& absum) {\n";
-  f << "    switch (fid) {\n";
-  for (size_t i = 0; i < reg.size(); ++i) f << "    case " << i << ": return qed_f_" << reg[i] << "<R>(z, absum);\n";
-  f << "    default: absum = 0.0; return R(0.0);\n    }\n}\n";
+  f << "};\n";
   fprintf(stderr, "qed_gen: %zu graphs, %ld terms, %ld monomials\n", reg.size(), st.terms, st.monos);
   return 0;
 }

@@ -1,0 +1,297 @@
+// Device side of qedmc: Philox4x32-10, the Eq. (1) point generator, the
+// integration / re-evaluation / dump / evaluation kernels.  Each kernel is a
+// template over the generated integrand id (FID) and the number of lines N;
+// one translation unit per generated graph instantiates them
+// (QED_DEFINE_KSET) so that the graphs compile in parallel.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qed_dd.cuh"
+
+template <int FID> struct qed_gen_f;   // specialised by the generated headers
+
+// ---------------------------------------------------------------------------
+// device: Philox4x32-10 and the uniform map
+// ---------------------------------------------------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ double u01(uint32_t hi, uint32_t lo) {
+  const uint64_t x = ((uint64_t(hi) << 32) | uint64_t(lo)) >> 11;
+  return (double(x) + 0.5) * 1.1102230246251565404e-16;   // 2^-53
+}
+
+struct KParams {
+  const double *F;        // F(S), 2^N
+  const double *G;        // F(S) / Deg(S), 2^N
+  const double *invdeg;   // 1 / Deg(S), 2^N
+  double logZ;            // log F(E)
+  uint64_t begin, n;
+  uint32_t key0, key1, stream;
+  double thresh;          // relative rounding-error threshold
+  // outputs
+  double *partials;       // [gridDim.x][4]: sum w (hi, lo), sum w^2 (hi, lo)
+  unsigned long long *counts;   // [gridDim.x][2]: flagged, unstable
+  unsigned long long *queue;    // flagged sample offsets
+  unsigned int *queue_len;
+  unsigned int queue_cap;
+  // dump mode
+  double *z_out, *f_out, *lp_out;
+  uint8_t *flag_out;
+};
+
+// Error model of the FP64 integrand: the forest terms are each computed to a
+// few ulps; their sum loses log2(sum|t| / |sum t|) bits.
+__device__ __forceinline__ double rel_err_estimate(double f, double absum, double ulp) {
+  return 16.0 * ulp * absum / fabs(f);
+}
+
+// Draw the point of sample `s`: z[line] (largest component 1) and log p.
+// Tables live in shared memory (sF, sG, sInv); xs is this thread's scratch
+// row in shared memory.
+template <int N>
+__device__ __forceinline__ double draw_point(uint64_t s, const KParams &P, const double *__restrict__ sF,
+                                             const double *__restrict__ sG, const double *__restrict__ sInv,
+                                             double *__restrict__ z) {
+  constexpr int ND = 2 * (N - 1);
+  double u[ND];
+#pragma unroll
+  for (int b = 0; b < (ND + 1) / 2; ++b) {
+    U4 w = philox4x32_10(U4{uint32_t(s), uint32_t(s >> 32), P.stream, uint32_t(b)}, P.key0, P.key1);
+    u[2 * b] = u01(w.x, w.y);
+    if (2 * b + 1 < ND) u[2 * b + 1] = u01(w.z, w.w);
+  }
+  const uint32_t full = (1u << N) - 1u;
+  uint32_t S = full;
+  int order[N];
+#pragma unroll
+  for (int l = 0; l < N - 1; ++l) {
+    const double target = u[l] * sF[S];
+    double cum = 0.0;
+    int pick = -1, last = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      if (pick < 0 && ((S >> j) & 1u)) {
+        cum += sG[S & ~(1u << j)];
+        last = j;
+        if (target < cum) pick = j;
+      }
+    }
+    if (pick < 0) pick = last;
+    order[l] = pick;
+    S &= ~(1u << pick);
+  }
+  order[N - 1] = __ffs(S) - 1;
+  // radial variables: t_l = u^(1/Deg(S_l)), z_{j_l} = z_{j_(l-1)} t_l
+  double lp = -P.logZ, logx = 0.0;
+  S = full;
+  double xs[N];
+  xs[0] = 1.0;
+#pragma unroll
+  for (int l = 1; l < N; ++l) {
+    S &= ~(1u << order[l - 1]);
+    const double lu = log(u[N - 1 + (l - 1)]);
+    logx += lu * sInv[S];
+    xs[l] = exp(logx);
+    lp += lu - logx;
+  }
+  // scatter sector order -> line index with constant register indices
+#pragma unroll
+  for (int L = 0; L < N; ++L) {
+    double v = 0.0;
+#pragma unroll
+    for (int l = 0; l < N; ++l) v = (order[l] == L) ? xs[l] : v;
+    z[L] = v;
+  }
+  return lp;
+}
+
+template <int N>
+__device__ __forceinline__ void load_tables(const KParams &P, double *sF, double *sG, double *sInv) {
+  for (int i = threadIdx.x; i < (1 << N); i += blockDim.x) {
+    sF[i] = P.F[i];
+    sG[i] = P.G[i];
+    sInv[i] = P.invdeg[i];
+  }
+  __syncthreads();
+}
+
+// Neumaier-compensated running sum
+struct KSum {
+  double s = 0.0, c = 0.0;
+  __device__ __forceinline__ void add(double x) {
+    const double t = s + x;
+    if (fabs(s) >= fabs(x)) c += (s - t) + x; else c += (x - t) + s;
+    s = t;
+  }
+};
+
+// Reduce (hi, lo) pairs of a block into partials[blockIdx.x]
+__device__ __forceinline__ void block_reduce_store(KSum a, KSum b, unsigned long long nf, unsigned long long nu,
+                                                   double *partials, unsigned long long *counts) {
+  dd x = dd_from_sum(a.s, a.c), y = dd_from_sum(b.s, b.c);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dd xo{__shfl_down_sync(0xffffffffu, x.hi, o), __shfl_down_sync(0xffffffffu, x.lo, o)};
+    dd yo{__shfl_down_sync(0xffffffffu, y.hi, o), __shfl_down_sync(0xffffffffu, y.lo, o)};
+    x = x + xo;
+    y = y + yo;
+    nf += __shfl_down_sync(0xffffffffu, nf, o);
+    nu += __shfl_down_sync(0xffffffffu, nu, o);
+  }
+  __shared__ double red[32][4];
+  __shared__ unsigned long long redc[32][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { red[warp][0] = x.hi; red[warp][1] = x.lo; red[warp][2] = y.hi; red[warp][3] = y.lo; redc[warp][0] = nf; redc[warp][1] = nu; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    dd X{0.0, 0.0}, Y{0.0, 0.0};
+    unsigned long long F = 0, Un = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+      X = X + dd{red[w][0], red[w][1]};
+      Y = Y + dd{red[w][2], red[w][3]};
+      F += redc[w][0];
+      Un += redc[w][1];
+    }
+    double *p = partials + 4 * blockIdx.x;
+    p[0] = X.hi; p[1] = X.lo; p[2] = Y.hi; p[3] = Y.lo;
+    counts[2 * blockIdx.x] = F;
+    counts[2 * blockIdx.x + 1] = Un;
+  }
+}
+
+// Main FP64 kernel: grid-stride over samples [begin, begin + n).
+template <int FID, int N>
+__global__ void __launch_bounds__(256) k_integrate(KParams P) {
+  extern __shared__ double smem[];
+  double *sF = smem, *sG = smem + (1 << N), *sInv = smem + 2 * (1 << N);
+  load_tables<N>(P, sF, sG, sInv);
+  KSum sw, sw2;
+  unsigned long long nflag = 0;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P.n; i += stride) {
+    const uint64_t s = P.begin + i;
+    double z[N];
+    const double lp = draw_point<N>(s, P, sF, sG, sInv, z);
+    double absum;
+    const double f = qed_gen_f<FID>::template eval<double>(z, absum);
+    const double w = f * exp(-lp);
+    const bool bad = !isfinite(w) || !(rel_err_estimate(f, absum, 1.1102230246251565e-16) <= P.thresh);
+    if (bad) {
+      ++nflag;
+      const unsigned int slot = atomicAdd(P.queue_len, 1u);
+      if (slot < P.queue_cap) P.queue[slot] = i;
+    } else {
+      sw.add(w);
+      sw2.add(w * w);
+    }
+  }
+  block_reduce_store(sw, sw2, nflag, 0ull, P.partials, P.counts);
+}
+
+// Double-double re-evaluation of flagged samples.  mode 0: the queue holds
+// the offsets; mode 1 (queue overflow): rescan every offset in [0, n) and
+// re-evaluate those the FP64 path flags.
+template <int FID, int N>
+__global__ void __launch_bounds__(256) k_redo_dd(KParams P, int mode, unsigned int qn) {
+  extern __shared__ double smem[];
+  double *sF = smem, *sG = smem + (1 << N), *sInv = smem + 2 * (1 << N);
+  load_tables<N>(P, sF, sG, sInv);
+  KSum sw, sw2;
+  unsigned long long nunst = 0;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  const uint64_t total = mode == 0 ? uint64_t(qn) : P.n;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const uint64_t off = mode == 0 ? P.queue[i] : i;
+    const uint64_t s = P.begin + off;
+    double z[N];
+    const double lp = draw_point<N>(s, P, sF, sG, sInv, z);
+    if (mode == 1) {
+      double ab;
+      const double f0 = qed_gen_f<FID>::template eval<double>(z, ab);
+      const double w0 = f0 * exp(-lp);
+      if (isfinite(w0) && rel_err_estimate(f0, ab, 1.1102230246251565e-16) <= P.thresh) continue;
+    }
+    dd zd[N];
+#pragma unroll
+    for (int L = 0; L < N; ++L) zd[L] = dd{z[L], 0.0};
+    double absum;
+    const dd f = qed_gen_f<FID>::template eval<dd>(zd, absum);
+    const double w = (f.hi + f.lo) * exp(-lp);
+    if (!isfinite(w) || !(rel_err_estimate(f.hi, absum, 1.2325951644078309e-32) <= P.thresh)) {
+      ++nunst;
+      continue;
+    }
+    sw.add(w);
+    sw2.add(w * w);
+  }
+  block_reduce_store(sw, sw2, 0ull, nunst, P.partials, P.counts);
+}
+
+template <int FID, int N>
+__global__ void __launch_bounds__(256) k_dump(KParams P) {
+  extern __shared__ double smem[];
+  double *sF = smem, *sG = smem + (1 << N), *sInv = smem + 2 * (1 << N);
+  load_tables<N>(P, sF, sG, sInv);
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P.n; i += stride) {
+    double z[N];
+    const double lp = draw_point<N>(P.begin + i, P, sF, sG, sInv, z);
+    double absum;
+    const double f = qed_gen_f<FID>::template eval<double>(z, absum);
+    const double w = f * exp(-lp);
+    uint8_t flag = 0;
+    if (!(rel_err_estimate(f, absum, 1.1102230246251565e-16) <= P.thresh)) flag |= 1;
+    if (!isfinite(w)) flag |= 2;
+#pragma unroll
+    for (int L = 0; L < N; ++L) P.z_out[i * N + L] = z[L];
+    P.f_out[i] = f;
+    P.lp_out[i] = lp;
+    P.flag_out[i] = flag;
+  }
+}
+
+template <int FID, int N>
+__global__ void __launch_bounds__(256) k_eval(const double *__restrict__ zin, uint64_t n, int prec, double *__restrict__ fout) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double absum;
+    if (prec == 0) {
+      double z[N];
+#pragma unroll
+      for (int L = 0; L < N; ++L) z[L] = zin[i * N + L];
+      fout[i] = qed_gen_f<FID>::template eval<double>(z, absum);
+    } else {
+      dd z[N];
+#pragma unroll
+      for (int L = 0; L < N; ++L) z[L] = dd{zin[i * N + L], 0.0};
+      const dd f = qed_gen_f<FID>::template eval<dd>(z, absum);
+      fout[i] = f.hi + f.lo;
+    }
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// per-graph kernel set
+// ---------------------------------------------------------------------------
+struct KernelSet {
+  const void *integrate, *redo, *dump, *eval;
+  int lines;
+};
+#define QED_DEFINE_KSET(id, lines)                                                              \
+  extern const KernelSet qed_kset_##id;                                                        \
+  const KernelSet qed_kset_##id = {(const void *)k_integrate<id, lines>, (const void *)k_redo_dd<id, lines>, \
+                                   (const void *)k_dump<id, lines>, (const void *)k_eval<id, lines>, lines};

@@ -1,0 +1,410 @@
+// qedmc: B300 (sm_103a) Monte Carlo integrator for the subtracted
+// Feynman-parametric integrands of lepton-loop-free QED vertex graphs
+// (arXiv:1905.08007, Sec. 2 and Sec. 3).  C ABI in include/qedmc.h.
+//
+// Hot path, one thread per sample, per launch:
+//   Philox4x32-10 draws (Sec. 3, Calc 2)
+//   -> Hepp-sector walk and radial variables of the Eq. (1) density
+//   -> generated FP64 integrand (forest-like subtraction, Sec. 2)
+//   -> rounding-error estimate; flagged points are queued for a
+//      double-double re-evaluation kernel (Sec. 3: arithmetics of different
+//      precisions)
+//   -> w = f / p accumulated per thread with Neumaier compensation, reduced
+//      with warp shuffles and shared memory to one double-double partial per
+//      block; the host folds the partials in a fixed order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "qedmc.h"
+#include "qed_graph.hpp"
+#include "qed_kernels.cuh"
+#include "qed_registry.h"
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+static int set_err(int code, const std::string &msg) { g_err = msg; return code; }
+#define CUDA_TRY(x)                                                                     \
+  do {                                                                                  \
+    cudaError_t e_ = (x);                                                               \
+    if (e_ != cudaSuccess) return set_err(QED_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+extern "C" const char *qed_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// kernel tables (one translation unit per generated graph defines qed_kset_<id>)
+// ---------------------------------------------------------------------------
+#define QED_DECL_KSET(id, lines) extern const KernelSet qed_kset_##id;
+QED_GENERATED_LIST(QED_DECL_KSET)
+#define QED_REF_KSET(id, lines) &qed_kset_##id,
+static const KernelSet *const g_kernels[] = {QED_GENERATED_LIST(QED_REF_KSET)};
+
+// ---------------------------------------------------------------------------
+// host objects
+// ---------------------------------------------------------------------------
+struct qed_ctx {
+  int device = 0;
+  cudaStream_t stream = 0;
+  int threads = 256;
+  int blocks = 0;            // 0 = 4 x SMs
+  int sms = 148;
+  double thresh = 1e-9;
+  // scratch owned by the context
+  double *partials = nullptr;
+  unsigned long long *counts = nullptr;
+  unsigned long long *queue = nullptr;
+  unsigned int *queue_len = nullptr;
+  unsigned int queue_cap = 1u << 22;
+  int partial_cap = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<double> h_partials;
+  std::vector<unsigned long long> h_counts;
+};
+
+struct qed_diag {
+  qed_ctx *ctx = nullptr;
+  qed::Graph g;
+  uint32_t stream_id = 0;
+  int fid = -1;
+  int N = 0;
+  double logZ = 0.0;
+  double *d_tab = nullptr;   // F, G, invdeg consecutively
+};
+
+static int ensure_scratch(qed_ctx *c, int blocks) {
+  if (blocks <= c->partial_cap) return QED_OK;
+  if (c->partials) cudaFree(c->partials);
+  if (c->counts) cudaFree(c->counts);
+  c->partials = nullptr; c->counts = nullptr;
+  CUDA_TRY(cudaMalloc(&c->partials, size_t(blocks) * 4 * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&c->counts, size_t(blocks) * 2 * sizeof(unsigned long long)));
+  c->partial_cap = blocks;
+  c->h_partials.resize(size_t(blocks) * 4);
+  c->h_counts.resize(size_t(blocks) * 2);
+  return QED_OK;
+}
+
+extern "C" int qed_ctx_create(int device, uint64_t flags, qed_ctx **out) {
+  (void)flags;
+  if (!out) return set_err(QED_EINVAL, "out is NULL");
+  int ndev = 0;
+  CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return set_err(QED_EINVAL, "no such device");
+  CUDA_TRY(cudaSetDevice(device));
+  qed_ctx *c = new qed_ctx();
+  c->device = device;
+  cudaDeviceProp prop;
+  CUDA_TRY(cudaGetDeviceProperties(&prop, device));
+  c->sms = prop.multiProcessorCount;
+  CUDA_TRY(cudaMalloc(&c->queue, size_t(c->queue_cap) * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&c->queue_len, sizeof(unsigned int)));
+  CUDA_TRY(cudaEventCreate(&c->ev0));
+  CUDA_TRY(cudaEventCreate(&c->ev1));
+  int rc = ensure_scratch(c, 8 * c->sms);
+  if (rc) return rc;
+  *out = c;
+  return QED_OK;
+}
+
+extern "C" int qed_ctx_destroy(qed_ctx *c) {
+  if (!c) return QED_OK;
+  cudaSetDevice(c->device);
+  if (c->partials) cudaFree(c->partials);
+  if (c->counts) cudaFree(c->counts);
+  if (c->queue) cudaFree(c->queue);
+  if (c->queue_len) cudaFree(c->queue_len);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  delete c;
+  return QED_OK;
+}
+
+extern "C" int qed_ctx_set_stream(qed_ctx *c, uintptr_t stream) {
+  if (!c) return set_err(QED_EINVAL, "ctx is NULL");
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  return QED_OK;
+}
+
+extern "C" int qed_ctx_set_launch(qed_ctx *c, int threads, int blocks) {
+  if (!c) return set_err(QED_EINVAL, "ctx is NULL");
+  if (threads < 32 || threads > 256 || threads % 32) return set_err(QED_EINVAL, "threads per block must be a multiple of 32 in [32, 256]");
+  if (blocks < 0 || blocks > 1 << 20) return set_err(QED_EINVAL, "blocks out of range");
+  c->threads = threads;
+  c->blocks = blocks;
+  return QED_OK;
+}
+
+extern "C" int qed_ctx_set_threshold(qed_ctx *c, double rel) {
+  if (!c || !(rel > 0.0)) return set_err(QED_EINVAL, "threshold must be > 0");
+  c->thresh = rel;
+  return QED_OK;
+}
+
+// ---------------------------------------------------------------------------
+// graphs
+// ---------------------------------------------------------------------------
+static bool to_graph(const qed_graph *in, qed::Graph &g, std::string &why) {
+  if (!in) { why = "graph is NULL"; return false; }
+  if (in->n < 1 || in->n > QED_MAX_LOOPS) { why = "loop order out of range"; return false; }
+  g = qed::Graph();
+  g.n = in->n;
+  g.e = in->e;
+  std::vector<int> seen(2 * g.n, 0);
+  for (int a = 0; a < g.n; ++a) {
+    int s = in->pairs[2 * a], t = in->pairs[2 * a + 1];
+    if (s < 0 || t < 0 || s >= 2 * g.n || t >= 2 * g.n || s == t) { why = "photon endpoint out of range"; return false; }
+    if (seen[s]++ || seen[t]++) { why = "vertex used twice"; return false; }
+    g.ph.push_back({std::min(s, t), std::max(s, t)});
+  }
+  std::sort(g.ph.begin(), g.ph.end());
+  if (g.e < 1 || g.e > 2 * g.n - 1) { why = "external vertex position out of range"; return false; }
+  if (!qed::admissible(g)) { why = "graph has a self-energy on an external leg or is one-particle reducible"; return false; }
+  return true;
+}
+
+static void from_graph(const qed::Graph &g, uint32_t id, qed_graph *o) {
+  std::memset(o, 0, sizeof *o);
+  o->n = g.n;
+  o->e = g.e;
+  for (int a = 0; a < g.n; ++a) { o->pairs[2 * a] = g.ph[a].first; o->pairs[2 * a + 1] = g.ph[a].second; }
+  o->stream_id = id;
+}
+
+extern "C" int qed_enumerate(int n, int reduced, qed_graph *out, int cap, int *count) {
+  if (n < 1 || n > QED_MAX_LOOPS || !count) return set_err(QED_EINVAL, "bad arguments");
+  auto gs = qed::enumerate_graphs(n);
+  std::vector<qed::Graph> sel;
+  if (!reduced) sel = gs;
+  else {
+    for (auto &g : gs) {
+      auto m = g.mirror();
+      if (g.key() <= m.key()) sel.push_back(g);
+    }
+  }
+  *count = int(sel.size());
+  for (int i = 0; i < std::min(cap, int(sel.size())); ++i) from_graph(sel[i], uint32_t(i), out + i);
+  return QED_OK;
+}
+
+extern "C" int qed_gauge_class(const qed_graph *in, int kmn[3]) {
+  qed::Graph g;
+  std::string why;
+  if (!to_graph(in, g, why)) return set_err(QED_EINVAL, why);
+  auto c = g.gauge_class();
+  kmn[0] = c[0]; kmn[1] = c[1]; kmn[2] = c[2];
+  return QED_OK;
+}
+
+extern "C" int qed_diagram_load(qed_ctx *ctx, const qed_graph *gin, const qed_pdf *pdf, qed_diag **out) {
+  if (!ctx || !out) return set_err(QED_EINVAL, "ctx/out is NULL");
+  qed::Graph g;
+  std::string why;
+  if (!to_graph(gin, g, why)) return set_err(QED_EINVAL, why);
+  int fid = -1;
+  const std::string nm = g.name();
+  for (int i = 0; i < QED_N_GENERATED; ++i) if (nm == qed_generated_names[i]) fid = i;
+  if (fid < 0) return set_err(QED_ENOTFOUND, "no generated integrand for " + nm);
+  const int N = g.n_lines();
+  const size_t M = size_t(1) << N;
+  std::vector<double> deg;
+  if (pdf && pdf->deg) {
+    deg.assign(pdf->deg, pdf->deg + M);
+    for (size_t m = 1; m + 1 < M; ++m)
+      if (!(deg[m] > 0.0) || !std::isfinite(deg[m])) return set_err(QED_EINVAL, "Deg must be positive and finite on every proper subset");
+  } else {
+    double c_div = (pdf && pdf->c_div > 0) ? pdf->c_div : 0.5;
+    double d_min = (pdf && pdf->d_min > 0) ? pdf->d_min : 0.05;
+    deg = qed::deg_table(g, c_div, d_min);
+  }
+  // F(S) = sum_{j in S, ascending} F(S \ j) / Deg(S \ j), F({x}) = 1
+  std::vector<double> F(M, 0.0), G(M, 0.0), inv(M, 0.0);
+  for (size_t m = 1; m < M; ++m) {
+    if (__builtin_popcountll(m) == 1) { F[m] = 1.0; continue; }
+    double acc = 0.0;
+    for (int j = 0; j < N; ++j) if (m >> j & 1) { size_t r = m & ~(size_t(1) << j); acc += F[r] / deg[r]; }
+    F[m] = acc;
+  }
+  for (size_t m = 1; m + 1 < M; ++m) { G[m] = F[m] / deg[m]; inv[m] = 1.0 / deg[m]; }
+  qed_diag *d = new qed_diag();
+  d->ctx = ctx; d->g = g; d->stream_id = gin->stream_id; d->fid = fid; d->N = N; d->logZ = std::log(F[M - 1]);
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  if (cudaMalloc(&d->d_tab, 3 * M * sizeof(double)) != cudaSuccess) { delete d; return set_err(QED_ENOMEM, "table allocation"); }
+  CUDA_TRY(cudaMemcpy(d->d_tab, F.data(), M * sizeof(double), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(d->d_tab + M, G.data(), M * sizeof(double), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(d->d_tab + 2 * M, inv.data(), M * sizeof(double), cudaMemcpyHostToDevice));
+  *out = d;
+  return QED_OK;
+}
+
+extern "C" int qed_diagram_free(qed_diag *d) {
+  if (!d) return QED_OK;
+  cudaSetDevice(d->ctx->device);
+  if (d->d_tab) cudaFree(d->d_tab);
+  delete d;
+  return QED_OK;
+}
+
+extern "C" int qed_diagram_info(const qed_diag *d, int *n_lines, int *fid, double *log_norm) {
+  if (!d) return set_err(QED_EINVAL, "diag is NULL");
+  if (n_lines) *n_lines = d->N;
+  if (fid) *fid = d->fid;
+  if (log_norm) *log_norm = d->logZ;
+  return QED_OK;
+}
+
+// ---------------------------------------------------------------------------
+// integration
+// ---------------------------------------------------------------------------
+static KParams base_params(const qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed) {
+  KParams P;
+  std::memset(&P, 0, sizeof P);
+  const size_t M = size_t(1) << d->N;
+  P.F = d->d_tab; P.G = d->d_tab + M; P.invdeg = d->d_tab + 2 * M;
+  P.logZ = d->logZ;
+  P.begin = begin; P.n = n;
+  P.key0 = uint32_t(seed); P.key1 = uint32_t(seed >> 32);
+  P.stream = d->stream_id;
+  P.thresh = d->ctx->thresh;
+  return P;
+}
+
+static int launch(const void *fn, int blocks, int threads, size_t smem, cudaStream_t st, void **args) {
+  CUDA_TRY(cudaLaunchKernel(fn, dim3(blocks), dim3(threads), args, smem, st));
+  return QED_OK;
+}
+
+static void dd_acc(double &hi, double &lo, double a_hi, double a_lo) {
+  // host double-double accumulate (hi, lo) += (a_hi, a_lo)
+  double s = hi + a_hi;
+  double bb = s - hi;
+  double err = (hi - (s - bb)) + (a_hi - bb);
+  err += lo + a_lo;
+  hi = s + err;
+  lo = err - (hi - s);
+}
+
+static int fold(qed_ctx *c, int blocks, qed_result *r, bool add_flagged_as_count) {
+  CUDA_TRY(cudaMemcpyAsync(c->h_partials.data(), c->partials, size_t(blocks) * 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaMemcpyAsync(c->h_counts.data(), c->counts, size_t(blocks) * 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  for (int b = 0; b < blocks; ++b) {
+    dd_acc(r->sum_w[0], r->sum_w[1], c->h_partials[4 * b], c->h_partials[4 * b + 1]);
+    dd_acc(r->sum_w2[0], r->sum_w2[1], c->h_partials[4 * b + 2], c->h_partials[4 * b + 3]);
+    if (add_flagged_as_count) r->n_flagged += c->h_counts[2 * b];
+    r->n_unstable += c->h_counts[2 * b + 1];
+  }
+  return QED_OK;
+}
+
+static void finish(qed_result *r) {
+  const double N = double(r->n);
+  if (r->n == 0) { r->value = 0.0; r->variance = 0.0; return; }
+  const double mean = (r->sum_w[0] + r->sum_w[1]) / N;
+  const double m2 = (r->sum_w2[0] + r->sum_w2[1]) / N;
+  r->value = mean;
+  r->variance = r->n > 1 ? std::max(0.0, m2 - mean * mean) / (N - 1.0) : 0.0;
+}
+
+extern "C" int qed_integrate_range(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed, qed_result *out) {
+  if (!d || !out) return set_err(QED_EINVAL, "diag/out is NULL");
+  qed_ctx *c = d->ctx;
+  CUDA_TRY(cudaSetDevice(c->device));
+  const KernelSet &K = *g_kernels[d->fid];
+  const int threads = c->threads;
+  const int blocks = c->blocks > 0 ? c->blocks : 4 * c->sms;
+  int rc = ensure_scratch(c, blocks);
+  if (rc) return rc;
+  const size_t smem = 3 * (size_t(1) << d->N) * sizeof(double);
+  qed_result r;
+  std::memset(&r, 0, sizeof r);
+  r.n = n;
+  CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+  const uint64_t chunk = uint64_t(1) << 30;
+  for (uint64_t off = 0; off < n; off += chunk) {
+    const uint64_t m = std::min(chunk, n - off);
+    KParams P = base_params(d, begin + off, m, seed);
+    P.partials = c->partials; P.counts = c->counts;
+    P.queue = c->queue; P.queue_len = c->queue_len; P.queue_cap = c->queue_cap;
+    CUDA_TRY(cudaMemsetAsync(c->queue_len, 0, sizeof(unsigned int), c->stream));
+    void *args[] = {&P};
+    if ((rc = launch(K.integrate, blocks, threads, smem, c->stream, args))) return rc;
+    if ((rc = fold(c, blocks, &r, true))) return rc;
+    unsigned int qn = 0;
+    CUDA_TRY(cudaMemcpy(&qn, c->queue_len, sizeof qn, cudaMemcpyDeviceToHost));
+    if (qn > 0) {
+      int mode = qn > c->queue_cap ? 1 : 0;
+      unsigned int qcount = std::min(qn, c->queue_cap);
+      void *args2[] = {&P, &mode, &qcount};
+      if ((rc = launch(K.redo, blocks, threads, smem, c->stream, args2))) return rc;
+      if ((rc = fold(c, blocks, &r, false))) return rc;
+    }
+  }
+  CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+  CUDA_TRY(cudaEventSynchronize(c->ev1));
+  float ms = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  r.seconds = ms * 1e-3;
+  finish(&r);
+  *out = r;
+  return QED_OK;
+}
+
+extern "C" int qed_integrate(qed_diag *d, uint64_t n, uint64_t seed, qed_result *out) {
+  return qed_integrate_range(d, 0, n, seed, out);
+}
+
+extern "C" int qed_dump_points(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed, double *z_dev, double *f_dev,
+                               double *lp_dev, uint8_t *flag_dev) {
+  if (!d || !z_dev || !f_dev || !lp_dev || !flag_dev) return set_err(QED_EINVAL, "NULL argument");
+  qed_ctx *c = d->ctx;
+  CUDA_TRY(cudaSetDevice(c->device));
+  KParams P = base_params(d, begin, n, seed);
+  P.z_out = z_dev; P.f_out = f_dev; P.lp_out = lp_dev; P.flag_out = flag_dev;
+  const int threads = c->threads;
+  const int blocks = int(std::max<uint64_t>(1, std::min<uint64_t>((n + threads - 1) / threads, uint64_t(c->sms) * 8)));
+  void *args[] = {&P};
+  int rc = launch(g_kernels[d->fid]->dump, blocks, threads, 3 * (size_t(1) << d->N) * sizeof(double), c->stream, args);
+  if (rc) return rc;
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return QED_OK;
+}
+
+extern "C" int qed_eval_points(qed_diag *d, const double *z_dev, uint64_t n, int prec, double *f_dev) {
+  if (!d || !z_dev || !f_dev || (prec != 0 && prec != 1)) return set_err(QED_EINVAL, "bad argument");
+  qed_ctx *c = d->ctx;
+  CUDA_TRY(cudaSetDevice(c->device));
+  const int threads = c->threads;
+  const int blocks = int(std::max<uint64_t>(1, std::min<uint64_t>((n + threads - 1) / threads, uint64_t(c->sms) * 8)));
+  void *args[] = {(void *)&z_dev, &n, &prec, &f_dev};
+  int rc = launch(g_kernels[d->fid]->eval, blocks, threads, 0, c->stream, args);
+  if (rc) return rc;
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return QED_OK;
+}
+
+extern "C" int qed_result_merge(const qed_result *a, const qed_result *b, qed_result *out) {
+  if (!a || !b || !out) return set_err(QED_EINVAL, "NULL argument");
+  qed_result r;
+  std::memset(&r, 0, sizeof r);
+  r.sum_w[0] = a->sum_w[0]; r.sum_w[1] = a->sum_w[1];
+  r.sum_w2[0] = a->sum_w2[0]; r.sum_w2[1] = a->sum_w2[1];
+  dd_acc(r.sum_w[0], r.sum_w[1], b->sum_w[0], b->sum_w[1]);
+  dd_acc(r.sum_w2[0], r.sum_w2[1], b->sum_w2[0], b->sum_w2[1]);
+  r.n = a->n + b->n;
+  r.n_flagged = a->n_flagged + b->n_flagged;
+  r.n_unstable = a->n_unstable + b->n_unstable;
+  r.seconds = a->seconds + b->seconds;
+  finish(&r);
+  *out = r;
+  return QED_OK;
+}
