@@ -19,7 +19,8 @@
  *  - Random numbers: Philox4x32-10 (Sec. 3, Calc 2), counter = (sample lo32,
  *    sample hi32, graph stream id, block), key = (seed lo32, seed hi32).
  *    Sample s uses draws 0..N-2 for the Hepp-sector walk and N-1..2N-3 for
- *    the radial variables, two draws per Philox block.  Results depend only
+ *    the radial variables, two draws per Philox block; draw = words (hi, lo)
+ *    -> ((((hi << 32) | lo) >> 12) + 0.5) * 2^-52, strictly inside (0,1).  Results depend only
  *    on (seed, stream id, sample range, launch shape).
  *  - All pointers are owned by the caller unless stated otherwise; the
  *    library copies what it keeps.  Device pointers must be on the context's

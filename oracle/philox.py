@@ -10,7 +10,9 @@ Stream layout used by both sides of this project (stated here as a
 definition, not shared code):
   counter = (sample lo32, sample hi32, diagram id, block), key = (seed lo32,
   seed hi32); draw d of a sample uses block d // 2, words 2*(d % 2) and
-  2*(d % 2) + 1; u = (((w_hi << 32) | w_lo) >> 11) + 0.5) * 2**-53 in (0,1).
+  2*(d % 2) + 1; u = ((((w_hi << 32) | w_lo) >> 12) + 0.5) * 2**-52: 52 random
+  bits, every value exactly representable and strictly inside (0,1) (a
+  53-bit version would round its top value to 1.0).
 """
 from __future__ import annotations
 
@@ -57,11 +59,11 @@ def philox_np(c0, c1, c2, c3, k0, k1):
 
 
 def words_to_uniform(w_hi, w_lo):
-    """Two 32-bit words -> one double in (0,1) with 53 random bits."""
+    """Two 32-bit words -> one double strictly inside (0,1), 52 random bits."""
     w_hi = np.asarray(w_hi, dtype=np.uint64)
     w_lo = np.asarray(w_lo, dtype=np.uint64)
-    x = ((w_hi << np.uint64(32)) | w_lo) >> np.uint64(11)
-    return (x.astype(np.float64) + 0.5) * 2.0 ** -53
+    x = ((w_hi << np.uint64(32)) | w_lo) >> np.uint64(12)
+    return (x.astype(np.float64) + 0.5) * 2.0 ** -52
 
 
 def uniforms(sample_idx, diagram_id: int, seed: int, n_draws: int):

@@ -29,8 +29,9 @@ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
 }
 
 __device__ __forceinline__ double u01(uint32_t hi, uint32_t lo) {
-  const uint64_t x = ((uint64_t(hi) << 32) | uint64_t(lo)) >> 11;
-  return (double(x) + 0.5) * 1.1102230246251565404e-16;   // 2^-53
+  // 52 random bits plus half a step: exactly representable, strictly in (0,1)
+  const uint64_t x = ((uint64_t(hi) << 32) | uint64_t(lo)) >> 12;
+  return (double(x) + 0.5) * 2.220446049250313080847e-16;   // 2^-52
 }
 
 struct KParams {
