@@ -1,0 +1,131 @@
+"""GPU parity tests through the C ABI: the CUDA path against the CPU oracle
+on the same Philox points (points, Eq. (1) density, integrand), sized to span
+several blocks and a ragged tail, plus sampled points at the end of the
+1e8-sample range the bench uses; estimator checks against A_1^(2) = 1/2.
+
+Tolerances: points and log p to 1e-12 (both sides draw the same counters and
+take the sector decisions in FP64 with the same tables and order; log/exp
+differ by ulps); integrand to 1e-12 relative on points whose rounding-error
+estimate is below the threshold (the forest terms cancel, so the error of
+both FP64 evaluations grows with sum|t|/|f|, which is what the flag bounds).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1905_08007_b300 as q                     # noqa: E402
+from oracle.graphs import deg_table, enumerate_graphs as o_enum   # noqa: E402
+from oracle.integrand import Integrand                 # noqa: E402
+from oracle.pdf import density, f_table, sample_points # noqa: E402
+from oracle.philox import uniforms                     # noqa: E402
+
+GRAPHS = [(1, 0)] + [(2, i) for i in range(6)]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return q.Context(0)
+
+
+def _oracle_points(og, stream, seed, begin, n):
+    N = og.n_lines
+    deg = deg_table(og)
+    F = f_table(deg, N)
+    u = uniforms(np.arange(begin, begin + n, dtype=np.uint64), stream, seed, 2 * (N - 1))
+    x, lp, _ = sample_points(u, deg, F, N)
+    return x, lp, deg, math.log(F[-1])
+
+
+@pytest.mark.parametrize("n,gi", GRAPHS)
+@pytest.mark.parametrize("begin,count", [(0, 1000 + 37), (10**8 - 333, 333)])
+def test_points_density_integrand_match_oracle(ctx, n, gi, begin, count):
+    g = q.enumerate_graphs(n)[gi]
+    og = o_enum(n)[gi]
+    d = ctx.load(g)
+    z, f, lp, fl = d.dump_points(begin, count, seed=0)
+    z, f, lp, fl = z.cpu().numpy(), f.cpu().numpy(), lp.cpu().numpy(), fl.cpu().numpy()
+    xo, lpo, deg, logZ = _oracle_points(og, g.stream_id, 0, begin, count)
+    # same sector for every point (an integer decision taken in FP64 on both sides)
+    assert np.array_equal(np.argsort(-z, axis=1, kind="stable"), np.argsort(-xo, axis=1, kind="stable"))
+    np.testing.assert_allclose(z, xo, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(lp, lpo, rtol=1e-12, atol=1e-12)
+    # density of Eq. (1) re-evaluated directly at the GPU's point
+    lpd = np.array([density(z[i], deg, logZ) for i in range(0, count, 7)])
+    np.testing.assert_allclose(lp[::7], lpd, rtol=1e-12, atol=1e-12)
+    # integrand at the GPU's own point
+    fo = Integrand(og)(z)
+    ok = fl == 0
+    assert ok.mean() > 0.95
+    rel = np.abs(f[ok] - fo[ok]) / np.abs(fo[ok])
+    assert rel.max() < 1e-12, rel.max()
+
+
+@pytest.mark.parametrize("n,gi", GRAPHS)
+def test_double_double_agrees_with_fp64_and_oracle(ctx, n, gi):
+    g = q.enumerate_graphs(n)[gi]
+    d = ctx.load(g)
+    z, f, lp, fl = d.dump_points(0, 512, seed=3)
+    fdd = d.eval_points(z, prec=1).cpu().numpy()
+    f64 = d.eval_points(z, prec=0).cpu().numpy()
+    np.testing.assert_array_equal(f64, f.cpu().numpy())
+    ok = fl.cpu().numpy() == 0
+    np.testing.assert_allclose(f64[ok], fdd[ok], rtol=1e-12)
+    fo = Integrand(o_enum(n)[gi])(z.cpu().numpy())
+    np.testing.assert_allclose(fdd[ok], fo[ok], rtol=1e-12)
+
+
+def test_one_loop_estimate_is_one_half(ctx):
+    d = ctx.load(q.enumerate_graphs(1)[0])
+    r = d.integrate(10**7, seed=0)
+    assert abs(r.value - 0.5) < 3 * r.sigma, (r.value, r.sigma)
+    assert r.n == 10**7 and r.n_unstable == 0
+
+
+def test_estimate_matches_oracle_sums_small(ctx):
+    """Same samples, same moments: GPU sum of w vs the oracle's."""
+    from oracle.estimator import mc_estimate
+    g = q.enumerate_graphs(2)[4]
+    d = ctx.load(g)
+    n = 20000 + 123
+    r = d.integrate(n, seed=5)
+    ro = mc_estimate(Integrand(o_enum(2)[4]), o_enum(2)[4], g.stream_id, 5, n)
+    assert r.value == pytest.approx(ro["value"], rel=1e-10)
+    assert r.variance == pytest.approx(ro["variance"], rel=1e-8)
+
+
+def test_replicas_merge_to_single_run(ctx):
+    d = ctx.load(q.enumerate_graphs(2)[1])
+    full = d.integrate(3_000_000, seed=9)
+    a = d.integrate(1_000_000, seed=9, begin=0)
+    b = d.integrate(2_000_000, seed=9, begin=1_000_000)
+    m = q.merge_results(a, b)
+    assert m.n == full.n
+    assert m.value == pytest.approx(full.value, rel=1e-12)
+    assert m.variance == pytest.approx(full.variance, rel=1e-10)
+
+
+def test_launch_shape_changes_only_rounding(ctx):
+    d = ctx.load(q.enumerate_graphs(2)[3])
+    r1 = d.integrate(500_000, seed=2)
+    ctx.set_launch(128, 97)
+    r2 = d.integrate(500_000, seed=2)
+    ctx.set_launch(256, 0)
+    assert r2.value == pytest.approx(r1.value, rel=1e-12)
+
+
+def test_empty_range_and_bad_arguments(ctx):
+    d = ctx.load(q.enumerate_graphs(1)[0])
+    r = d.integrate(0, seed=0)
+    assert r.n == 0 and r.value == 0.0
+    with pytest.raises(q.QedError):
+        ctx.set_launch(100, 0)
+    with pytest.raises(q.QedError):
+        ctx.load(q.Graph(2, ((0, 1), (2, 3)), 2))
+    with pytest.raises(q.QedError):
+        ctx.load(q.enumerate_graphs(1)[0], deg=np.zeros(8))
