@@ -80,7 +80,9 @@ typedef struct {
   uint64_t n;                     /* samples */
   uint64_t n_flagged;             /* points re-evaluated in double-double */
   uint64_t n_unstable;            /* points unstable in double-double: w := 0 */
-  double seconds;                 /* device time of the call */
+  double seconds;                 /* device time of the call (all kernels) */
+  double kernel_seconds;          /* device time of the FP64 integration kernel */
+  uint32_t launches;              /* kernels launched by the call */
 } qed_result;
 
 /* ---- context ------------------------------------------------------------ */
@@ -91,11 +93,13 @@ int qed_ctx_destroy(qed_ctx *ctx);
 /* Launch subsequent work on this cudaStream_t (0 = legacy default stream). */
 int qed_ctx_set_stream(qed_ctx *ctx, uintptr_t stream);
 /* Launch shape of the integration kernels: threads per block (multiple of 32,
- * <= 1024) and blocks (0 = 4 x the SM count).  Results depend on it through
+ * 32..256) and blocks (0 = 4 x the SM count).  Results depend on it through
  * the summation order only. */
 int qed_ctx_set_launch(qed_ctx *ctx, int threads_per_block, int blocks);
 /* Relative rounding-error threshold above which a point is re-evaluated in
- * double-double (Sec. 3: arithmetics of different precisions).  Default 1e-9. */
+ * double-double (Sec. 3: arithmetics of different precisions).  Default 1e-12.
+ * The estimate is 16 ulp x (sum of the absolute values of the integrand's
+ * monomials) / |f|. */
 int qed_ctx_set_threshold(qed_ctx *ctx, double rel_err);
 const char *qed_last_error(void);
 
@@ -135,9 +139,18 @@ int qed_dump_points(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed,
  * (prec = 0) or double-double (prec = 1, result rounded to double). */
 int qed_eval_points(qed_diag *d, const double *z_dev, uint64_t n, int prec, double *f_dev);
 
-/* Merge replica results (Chan et al. pairwise update of the moments in
- * double-double, fixed order): out = a (+) b. */
+/* Merge replica results over disjoint sample ranges: the raw moments add in
+ * double-double, so the merge is exact and order-fixed: out = a (+) b. */
 int qed_result_merge(const qed_result *a, const qed_result *b, qed_result *out);
+
+/* ---- measurement -------------------------------------------------------- */
+/* FP64 arithmetic operations (add, sub, mul, div; transcendental functions
+ * counted once each) per sample of this graph's hot path: sampler, integrand
+ * and accumulation.  Used as the algorithmic work of the roofline. */
+int qed_diagram_flops(const qed_diag *d, double *flops_per_sample);
+/* Measured FP64 fused-multiply-add throughput of the device (FLOP/s, 2 per
+ * FMA): every SM runs independent FMA chains for about `ms` milliseconds. */
+int qed_fp64_peak(int device, double ms, double *flops_per_s);
 
 #ifdef __cplusplus
 }

@@ -18,4 +18,5 @@ from ._lib import (  # noqa: F401
     lib_path,
     load_library,
     merge_results,
+    fp64_peak,
 )

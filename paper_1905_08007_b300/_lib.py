@@ -39,7 +39,8 @@ class _Pdf(C.Structure):
 class _Result(C.Structure):
     _fields_ = [("value", C.c_double), ("variance", C.c_double), ("sum_w", C.c_double * 2),
                 ("sum_w2", C.c_double * 2), ("n", C.c_uint64), ("n_flagged", C.c_uint64),
-                ("n_unstable", C.c_uint64), ("seconds", C.c_double)]
+                ("n_unstable", C.c_uint64), ("seconds", C.c_double),
+                ("kernel_seconds", C.c_double), ("launches", C.c_uint32)]
 
 
 @dataclass(frozen=True)
@@ -77,6 +78,8 @@ class Result:
     n_flagged: int
     n_unstable: int
     seconds: float
+    kernel_seconds: float = 0.0
+    launches: int = 0
 
     @property
     def sigma(self):
@@ -88,12 +91,13 @@ class Result:
         r.sum_w[0], r.sum_w[1] = self.sum_w
         r.sum_w2[0], r.sum_w2[1] = self.sum_w2
         r.n, r.n_flagged, r.n_unstable, r.seconds = self.n, self.n_flagged, self.n_unstable, self.seconds
+        r.kernel_seconds, r.launches = self.kernel_seconds, self.launches
         return r
 
     @staticmethod
     def _from_c(r):
         return Result(r.value, r.variance, (r.sum_w[0], r.sum_w[1]), (r.sum_w2[0], r.sum_w2[1]),
-                      r.n, r.n_flagged, r.n_unstable, r.seconds)
+                      r.n, r.n_flagged, r.n_unstable, r.seconds, r.kernel_seconds, r.launches)
 
 
 _LIB = None
@@ -131,6 +135,8 @@ def load_library():
                                       C.c_void_p, C.c_void_p, C.c_void_p]),
         "qed_eval_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_void_p]),
         "qed_result_merge": (C.c_int, [P(_Result), P(_Result), P(_Result)]),
+        "qed_diagram_flops": (C.c_int, [C.c_void_p, P(C.c_double)]),
+        "qed_fp64_peak": (C.c_int, [C.c_int, C.c_double, P(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -160,6 +166,13 @@ def gauge_class(g: Graph):
     cg = g._c()
     _check(L.qed_gauge_class(C.byref(cg), out))
     return tuple(out)
+
+
+def fp64_peak(device: int = 0, ms: float = 50.0) -> float:
+    """Measured FP64 FMA throughput of the device in FLOP/s."""
+    v = C.c_double()
+    _check(load_library().qed_fp64_peak(device, ms, C.byref(v)))
+    return v.value
 
 
 def merge_results(a: Result, b: Result) -> Result:
@@ -258,6 +271,11 @@ class Diagram:
         torch.cuda.synchronize(z.device)
         _check(load_library().qed_eval_points(self._h, z.data_ptr(), z.shape[0], prec, f.data_ptr()))
         return f
+
+    def flops_per_sample(self) -> float:
+        v = C.c_double()
+        _check(load_library().qed_diagram_flops(self._h, C.byref(v)))
+        return v.value
 
     def close(self):
         if self._h:

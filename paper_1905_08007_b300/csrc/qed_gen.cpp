@@ -580,11 +580,24 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
     Bc[key] = v;
     return v;
   };
-  // block values: recursive, returns vector of variable names per k
-  std::function<std::vector<std::string>(int)> block_val = [&](int bi) -> std::vector<std::string> {
+  // |A|, |C|, |K| in FP32 for the condition estimate (all lie in [-1, 1]
+  // up to O(1) factors, so single precision has the range and accuracy an
+  // estimate needs; FP32 is the cheap pipe)
+  std::map<std::string, std::string> fabs_cache;
+  auto fabsvar = [&](const std::string &v) -> std::string {
+    auto it = fabs_cache.find(v);
+    if (it != fabs_cache.end()) return it->second;
+    std::string fv = "fa_" + v;
+    os << "    const float " << fv << " = fabsf(float(to_double(" << v << ")));\n";
+    fabs_cache[v] = fv;
+    return fv;
+  };
+  // block values: recursive, returns (value, absolute-sum) variable names per k
+  typedef std::pair<std::vector<std::string>, std::vector<std::string>> VA;
+  std::function<VA(int)> block_val = [&](int bi) -> VA {
     const Block &B = T.t.blocks[bi];
     const auto &seq = T.seq[bi];
-    std::vector<std::vector<std::string>> childv;
+    std::vector<VA> childv;
     for (int c : B.children) childv.push_back(block_val(c));
     // momentum factors
     std::vector<int> mom_items;
@@ -620,6 +633,7 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
     for (int i = 0; i < m; ++i) all[i] = i;
     rec(all, {});
     std::map<int, std::string> ownk;    // k -> accumulated expression variable
+    std::map<int, std::string> ownk_abs;  // k -> accumulated absolute sum (double)
     for (auto &pat : pats) {
       // B product
       std::string bprod;
@@ -642,17 +656,18 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
       for (auto &pp : ph_pairs) { D.pair_partner[pp.first] = pp.second; D.pair_partner[pp.second] = pp.first; }
       for (auto &pr : pat) { int a = mom_items[pr.first], b = mom_items[pr.second]; D.pair_partner[a] = b; D.pair_partner[b] = a; }
       D.go(0, mono_identity(), -1, -1, 0u, -1);
-      std::string poly;
+      std::string poly, apoly;
       for (auto &kv : D.acc) {
         cd c = kv.second;
         if (std::abs(c.imag()) > 1e-9 * (1 + std::abs(c.real()))) { fprintf(stderr, "complex coefficient %g %g\n", c.real(), c.imag()); exit(1); }
         double cr = snap(c.real());
         if (cr == 0.0) continue;
-        std::string mono;
+        std::string mono, amono;
         for (int f = 0; f < m; ++f) if (kv.first.pmask >> f & 1) {
           const std::string &v = A[mom_line[f]];
           if (v.empty()) { mono = "ZERO"; break; }
           mono += " * " + v;
+          amono += " * " + fabsvar(v);
         }
         if (mono == "ZERO") continue;
         if (kv.first.deriv >= 0) {
@@ -660,46 +675,66 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
           const std::string &v = (B.proj == PR_F2) ? C[mom_line[f]] : K[mom_line[f]];
           if (v.empty()) continue;
           mono += " * " + v;
+          amono += " * " + fabsvar(v);
         }
         poly += (poly.empty() ? "R(" : " + R(") + dstr(cr) + ")" + mono;
+        apoly += std::string(apoly.empty() ? "" : " + ") + dstr(std::abs(cr)) + "f" + amono;
         ++st.monos;
       }
       if (poly.empty()) continue;
       int k = int(pat.size());
       std::string var = P + "_b" + std::to_string(bi) + "k" + std::to_string(k);
       std::string contrib = bprod.empty() ? "(" + poly + ")" : bprod + " * (" + poly + ")";
-      if (!ownk.count(k)) { os << "    R " << var << " = " << contrib << ";\n"; ownk[k] = var; }
-      else os << "    " << var << " = " << var << " + " << contrib << ";\n";
+      std::string acontrib = bprod.empty() ? "double(" + apoly + ")" : "fabs(to_double(" + bprod + ")) * double(" + apoly + ")";
+      std::string avar = var + "_a";
+      if (!ownk.count(k)) {
+        os << "    R " << var << " = " << contrib << ";\n";
+        os << "    double " << avar << " = " << acontrib << ";\n";
+        ownk[k] = var; ownk_abs[k] = avar;
+      } else {
+        os << "    " << var << " = " << var << " + " << contrib << ";\n";
+        os << "    " << avar << " = " << avar << " + " << acontrib << ";\n";
+      }
     }
     int kmax = ownk.empty() ? 0 : ownk.rbegin()->first;
-    std::vector<std::string> vals(kmax + 1);
-    for (int k = 0; k <= kmax; ++k) vals[k] = ownk.count(k) ? ownk[k] : "";
-    for (auto &cv : childv) {
-      std::vector<std::string> nv(vals.size() + cv.size() - 1);
+    std::vector<std::string> vals(kmax + 1), avals(kmax + 1);
+    for (int k = 0; k <= kmax; ++k) { vals[k] = ownk.count(k) ? ownk[k] : ""; avals[k] = ownk_abs.count(k) ? ownk_abs[k] : ""; }
+    for (auto &cva : childv) {
+      const auto &cv = cva.first, &ca = cva.second;
+      std::vector<std::string> nv(vals.size() + cv.size() - 1), na(vals.size() + cv.size() - 1);
       for (size_t i = 0; i < vals.size(); ++i) for (size_t j = 0; j < cv.size(); ++j) {
         if (vals[i].empty() || cv[j].empty()) continue;
         std::string v = P + "_c" + std::to_string(bi) + "_" + std::to_string(E.tmp++);
         os << "    const R " << v << " = " << vals[i] << " * " << cv[j] << ";\n";
+        os << "    const double " << v << "_a = " << avals[i] << " * " << ca[j] << ";\n";
         nv[i + j] = nv[i + j].empty() ? v : "(" + nv[i + j] + " + " + v + ")";
+        na[i + j] = na[i + j].empty() ? v + "_a" : "(" + na[i + j] + " + " + v + "_a)";
       }
       vals = nv;
+      avals = na;
     }
-    return vals;
+    return VA(vals, avals);
   };
-  auto vals = block_val(0);
+  auto va = block_val(0);
+  auto &vals = va.first;
+  auto &avals = va.second;
   // combine: (-1)^n 4^-n sum_k (-1)^k Gamma(n-k) U^-2 V^(k-n) (2U)^-k val_k
   os << "    const R " << P << "_iV = R(1.0) / " << V << ";\n";
-  std::string acc;
+  std::string acc, aacc;
   for (int k = 0; k < n && k < int(vals.size()); ++k) {
     if (vals[k].empty()) continue;
     double c = ((n + k) % 2 ? -1.0 : 1.0) * std::tgamma(double(n - k)) * std::pow(4.0, -n) * std::pow(2.0, -k);
     std::string f = "R(" + dstr(c) + ")";
     for (int i = 0; i < n - k; ++i) f += " * " + P + "_iV";
     for (int i = 0; i < 2 + k; ++i) f += " * " + P + "_iU";
-    acc += (acc.empty() ? "" : " + ") + f + " * " + vals[k];
+    std::string fk = P + "_f" + std::to_string(k);
+    os << "    const R " << fk << " = " << f << ";\n";
+    acc += (acc.empty() ? "" : " + ") + fk + " * " + vals[k];
+    aacc += std::string(aacc.empty() ? "" : " + ") + "fabs(to_double(" + fk + ")) * " + avals[k];
   }
-  if (acc.empty()) acc = "R(0.0)";
+  if (acc.empty()) { acc = "R(0.0)"; aacc = "0.0"; }
   os << "    const R " << out << " = R(" << T.t.sign << ".0) * (" << acc << ");\n";
+  os << "    const double " << out << "_abs = " << aacc << ";\n";
   ++st.terms;
 }
 
@@ -711,10 +746,12 @@ int main(int argc, char **argv) {
   const char *banner =
       "// Generated by qed_gen from the forest-like subtraction formula. Do not edit.\n"
       "// Subtracted Feynman-parametric integrand of one vertex graph, homogeneous\n"
-      "// of degree -3n in z; absum receives the sum of the absolute values of the\n"
-      "// forest terms (the cancellation measure used by the rounding-error flag).\n";
+      "// of degree -3n in z; absum receives the sum of the absolute values of all\n"
+      "// its monomials (the cancellation measure used by the rounding-error flag;\n"
+      "// the magnitudes of the Q coefficients are taken in FP32).\n";
   std::vector<std::string> reg;
   std::vector<int> reg_lines;
+  std::vector<long> reg_flops;
   GenStats st;
   for (int ai = 2; ai < argc; ++ai) {
     int n = atoi(argv[ai]);
@@ -731,13 +768,23 @@ int main(int argc, char **argv) {
         outs.push_back(o);
       }
       const int id = int(reg.size());
+      // algorithmic FP64 operations of the integrand: binary operators in the
+      // emitted expressions plus the absum accumulation and the final sum
+      {
+        const std::string body = E.os.str();
+        long ops = 0;
+        for (size_t k = 0; k + 2 < body.size(); ++k)
+          if (body[k] == ' ' && body[k + 2] == ' ' && (body[k + 1] == '+' || body[k + 1] == '-' || body[k + 1] == '*' || body[k + 1] == '/')) ++ops;
+        ops += 3 * long(outs.size());
+        reg_flops.push_back(ops);
+      }
       std::ofstream f(dir + "/g_" + std::to_string(id) + ".cuh");
       f << banner << "#pragma once\n\n";
       f << "// " << g.name() << ": " << terms.size() << " forest terms\n";
       f << "template <class R>\n__device__ __forceinline__ R qed_f_" << g.name() << "(const R* __restrict__ z, double& absum) {\n";
       f << E.os.str();
       f << "    absum = 0.0;\n";
-      for (auto &o : outs) f << "    absum += fabs(to_double(" << o << "));\n";
+      for (auto &o : outs) f << "    absum += " << o << "_abs;\n";
       f << "    return ";
       for (size_t i = 0; i < outs.size(); ++i) f << (i ? " + " : "") << outs[i];
       f << ";\n}\n\n";
@@ -753,6 +800,9 @@ int main(int argc, char **argv) {
   f << "// X(id, lines)\n#define QED_GENERATED_LIST(X)";
   for (size_t i = 0; i < reg.size(); ++i) f << " X(" << i << ", " << reg_lines[i] << ")";
   f << "\n";
+  f << "static const double qed_generated_flops[] = {";
+  for (size_t i = 0; i < reg.size(); ++i) f << (i ? ", " : "") << reg_flops[i] << ".0";
+  f << "};\n";
   f << "static const char* const qed_generated_names[] = {";
   for (size_t i = 0; i < reg.size(); ++i) f << (i ? ", " : "") << "\"" << reg[i] << "\"";
   f << "};\n";

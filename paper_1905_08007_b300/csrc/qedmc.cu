@@ -58,7 +58,7 @@ struct qed_ctx {
   int threads = 256;
   int blocks = 0;            // 0 = 4 x SMs
   int sms = 148;
-  double thresh = 1e-9;
+  double thresh = 1e-12;
   // scratch owned by the context
   double *partials = nullptr;
   unsigned long long *counts = nullptr;
@@ -66,7 +66,7 @@ struct qed_ctx {
   unsigned int *queue_len = nullptr;
   unsigned int queue_cap = 1u << 22;
   int partial_cap = 0;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk0 = nullptr, evk1 = nullptr;
   std::vector<double> h_partials;
   std::vector<unsigned long long> h_counts;
 };
@@ -110,6 +110,8 @@ extern "C" int qed_ctx_create(int device, uint64_t flags, qed_ctx **out) {
   CUDA_TRY(cudaMalloc(&c->queue_len, sizeof(unsigned int)));
   CUDA_TRY(cudaEventCreate(&c->ev0));
   CUDA_TRY(cudaEventCreate(&c->ev1));
+  CUDA_TRY(cudaEventCreate(&c->evk0));
+  CUDA_TRY(cudaEventCreate(&c->evk1));
   int rc = ensure_scratch(c, 8 * c->sms);
   if (rc) return rc;
   *out = c;
@@ -125,6 +127,8 @@ extern "C" int qed_ctx_destroy(qed_ctx *c) {
   if (c->queue_len) cudaFree(c->queue_len);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->evk0) cudaEventDestroy(c->evk0);
+  if (c->evk1) cudaEventDestroy(c->evk1);
   delete c;
   return QED_OK;
 }
@@ -337,8 +341,14 @@ extern "C" int qed_integrate_range(qed_diag *d, uint64_t begin, uint64_t n, uint
     P.queue = c->queue; P.queue_len = c->queue_len; P.queue_cap = c->queue_cap;
     CUDA_TRY(cudaMemsetAsync(c->queue_len, 0, sizeof(unsigned int), c->stream));
     void *args[] = {&P};
+    CUDA_TRY(cudaEventRecord(c->evk0, c->stream));
     if ((rc = launch(K.integrate, blocks, threads, smem, c->stream, args))) return rc;
+    CUDA_TRY(cudaEventRecord(c->evk1, c->stream));
+    ++r.launches;
     if ((rc = fold(c, blocks, &r, true))) return rc;
+    float kms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&kms, c->evk0, c->evk1));
+    r.kernel_seconds += kms * 1e-3;
     unsigned int qn = 0;
     CUDA_TRY(cudaMemcpy(&qn, c->queue_len, sizeof qn, cudaMemcpyDeviceToHost));
     if (qn > 0) {
@@ -346,6 +356,7 @@ extern "C" int qed_integrate_range(qed_diag *d, uint64_t begin, uint64_t n, uint
       unsigned int qcount = std::min(qn, c->queue_cap);
       void *args2[] = {&P, &mode, &qcount};
       if ((rc = launch(K.redo, blocks, threads, smem, c->stream, args2))) return rc;
+      ++r.launches;
       if ((rc = fold(c, blocks, &r, false))) return rc;
     }
   }
@@ -404,7 +415,70 @@ extern "C" int qed_result_merge(const qed_result *a, const qed_result *b, qed_re
   r.n_flagged = a->n_flagged + b->n_flagged;
   r.n_unstable = a->n_unstable + b->n_unstable;
   r.seconds = a->seconds + b->seconds;
+  r.kernel_seconds = a->kernel_seconds + b->kernel_seconds;
+  r.launches = a->launches + b->launches;
   finish(&r);
   *out = r;
+  return QED_OK;
+}
+
+// ---------------------------------------------------------------------------
+// measurement helpers
+// ---------------------------------------------------------------------------
+extern "C" int qed_diagram_flops(const qed_diag *d, double *flops) {
+  if (!d || !flops) return set_err(QED_EINVAL, "NULL argument");
+  const double N = d->N;
+  // sampler: uniform map (2 per draw), walk (target product and on average
+  // half of the running sums per level), radial (log, scale, running sum,
+  // exp, density update), weight (exp, product), accumulation (square and
+  // two compensated sums)
+  const double sampler = 4.0 * (N - 1) + (N - 1) + (N - 1) * (N + 2) / 4.0 + 6.0 * (N - 1) + 2.0 + 9.0;
+  *flops = qed_generated_flops[d->fid] + sampler;
+  return QED_OK;
+}
+
+__global__ void k_fp64_peak(double *out, int iters, double b, double c) {
+  double a[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = 1e-3 * (threadIdx.x + 1) + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = fma(a[i], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) s += a[i];
+  if (s == -1.2345e300) out[0] = s;   // keeps the chains live
+}
+
+extern "C" int qed_fp64_peak(int device, double ms, double *flops) {
+  if (!flops || !(ms > 0)) return set_err(QED_EINVAL, "bad argument");
+  CUDA_TRY(cudaSetDevice(device));
+  cudaDeviceProp prop;
+  CUDA_TRY(cudaGetDeviceProperties(&prop, device));
+  double *out = nullptr;
+  CUDA_TRY(cudaMalloc(&out, sizeof(double)));
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  const int threads = 256, blocks = prop.multiProcessorCount * 8;
+  int iters = 1 << 12;
+  double best = 0.0;
+  for (int rep = 0; rep < 8; ++rep) {
+    CUDA_TRY(cudaEventRecord(e0));
+    k_fp64_peak<<<blocks, threads>>>(out, iters, 0.99999999, 1e-9);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventRecord(e1));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    float t = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+    const double f = 2.0 * 16.0 * double(iters) * threads * blocks / (t * 1e-3);
+    best = std::max(best, f);
+    if (t < 0.5 * ms && iters < (1 << 24)) iters *= 2;   // grow until the launch lasts about ms
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  *flops = best;
   return QED_OK;
 }
