@@ -451,6 +451,92 @@ static std::string zsum(const std::vector<int> &ls) {
   return s;
 }
 
+// ---------------------------------------------------------------------------
+// symbolic polynomials in the Feynman parameters (dyadic-rational
+// coefficients, exact in binary floating point)
+// ---------------------------------------------------------------------------
+struct Poly {
+  std::map<std::vector<int>, double> t;     // sorted variable multiset -> coefficient
+  static Poly var(int l) { Poly p; p.t[{l}] = 1.0; return p; }
+  static Poly cst(double c) { Poly p; if (c != 0.0) p.t[{}] = c; return p; }
+  bool zero() const { return t.empty(); }
+  void clean() { for (auto it = t.begin(); it != t.end();) { if (it->second == 0.0) it = t.erase(it); else ++it; } }
+  Poly operator+(const Poly &o) const { Poly r = *this; for (auto &kv : o.t) r.t[kv.first] += kv.second; r.clean(); return r; }
+  Poly operator-(const Poly &o) const { Poly r = *this; for (auto &kv : o.t) r.t[kv.first] -= kv.second; r.clean(); return r; }
+  Poly operator*(double c) const { Poly r; if (c == 0.0) return r; for (auto &kv : t) r.t[kv.first] = kv.second * c; return r; }
+  Poly operator*(const Poly &o) const {
+    Poly r;
+    for (auto &a : t) for (auto &b : o.t) {
+      std::vector<int> m = a.first;
+      m.insert(m.end(), b.first.begin(), b.first.end());
+      std::sort(m.begin(), m.end());
+      r.t[m] += a.second * b.second;
+    }
+    r.clean();
+    return r;
+  }
+  // nested (Horner-like) form: factor out the most frequent variable
+  std::string horner() const {
+    if (t.empty()) return "R(0.0)";
+    std::map<int, int> freq;
+    for (auto &kv : t) { std::set<int> u(kv.first.begin(), kv.first.end()); for (int v : u) ++freq[v]; }
+    if (freq.empty()) return "R(" + dstr(t.begin()->second) + ")";
+    int best = -1, bc = 0;
+    for (auto &kv : freq) if (kv.second > bc) { bc = kv.second; best = kv.first; }
+    Poly with, without;
+    for (auto &kv : t) {
+      auto it = std::find(kv.first.begin(), kv.first.end(), best);
+      if (it == kv.first.end()) { without.t[kv.first] = kv.second; continue; }
+      std::vector<int> m = kv.first;
+      m.erase(m.begin() + (it - kv.first.begin()));
+      with.t[m] = kv.second;
+    }
+    std::string zv = "z[" + std::to_string(best) + "]";
+    std::string inner;
+    if (with.t.size() == 1 && with.t.begin()->first.empty()) {
+      double c = with.t.begin()->second;
+      inner = (c == 1.0) ? zv : "R(" + dstr(c) + ") * " + zv;
+    } else {
+      inner = zv + " * (" + with.horner() + ")";
+    }
+    if (without.zero()) return inner;
+    return inner + " + " + without.horner();
+  }
+};
+
+static Poly det_poly(const std::vector<std::vector<Poly>> &m) {
+  const int n = int(m.size());
+  if (n == 0) return Poly::cst(1.0);
+  if (n == 1) return m[0][0];
+  Poly r;
+  for (int c = 0; c < n; ++c) {
+    if (m[0][c].zero()) continue;
+    std::vector<std::vector<Poly>> sub;
+    for (int i = 1; i < n; ++i) {
+      std::vector<Poly> row;
+      for (int j = 0; j < n; ++j) if (j != c) row.push_back(m[i][j]);
+      sub.push_back(row);
+    }
+    Poly d = m[0][c] * det_poly(sub);
+    r = (c % 2) ? r - d : r + d;
+  }
+  return r;
+}
+
+// (-1)^(r+c) det(m without row r and column c)
+static Poly cofactor_poly(const std::vector<std::vector<Poly>> &m, int r, int c) {
+  const int n = int(m.size());
+  std::vector<std::vector<Poly>> sub;
+  for (int i = 0; i < n; ++i) {
+    if (i == r) continue;
+    std::vector<Poly> row;
+    for (int j = 0; j < n; ++j) if (j != c) row.push_back(m[i][j]);
+    sub.push_back(row);
+  }
+  Poly d = det_poly(sub);
+  return ((r + c) % 2) ? d * -1.0 : d;
+}
+
 struct GenStats { long terms = 0, monos = 0; };
 
 // Emits code computing one term's value into variable `out` (declared here).
@@ -459,111 +545,57 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
   int n = g.n, L = g.n_lines();
   auto &os = E.os;
   std::string P = E.fresh("t");
-  // Lambda entries
-  std::vector<std::vector<std::string>> lam(n, std::vector<std::string>(n));
+  // Graph polynomials, expanded symbolically so that every cancellation
+  // between monomials happens here, exactly, and the device evaluates
+  // polynomials whose terms do not cancel (U, B_ij, U V have non-negative
+  // coefficients; U A_l too on lines carrying the external momentum).
+  std::vector<std::vector<Poly>> lam(n, std::vector<Poly>(n));
   for (int a = 0; a < n; ++a)
-    for (int b = a; b < n; ++b) {
-      std::vector<int> ls;
-      for (int l = 0; l < L; ++l) if (T.eta[l][a] && T.eta[l][b]) ls.push_back(l);
-      if (ls.empty()) { lam[a][b] = lam[b][a] = ""; continue; }
-      std::string v = P + "_L" + std::to_string(a) + std::to_string(b);
-      os << "    const R " << v << " = " << zsum(ls) << ";\n";
-      lam[a][b] = lam[b][a] = v;
-    }
-  // determinant and adjugate (cofactors), n <= 3 written out
-  auto L_ = [&](int a, int b) -> std::string { return lam[a][b].empty() ? "R(0.0)" : lam[a][b]; };
-  std::vector<std::vector<std::string>> adj(n, std::vector<std::string>(n));
+    for (int b = 0; b < n; ++b)
+      for (int l = 0; l < L; ++l) if (T.eta[l][a] && T.eta[l][b]) lam[a][b] = lam[a][b] + Poly::var(l);
+  Poly Up = det_poly(lam);
+  std::vector<std::vector<Poly>> adjp(n, std::vector<Poly>(n));
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) adjp[a][b] = cofactor_poly(lam, b, a);
   std::string U = P + "_U";
-  if (n == 1) {
-    os << "    const R " << U << " = " << L_(0, 0) << ";\n";
-    adj[0][0] = "R(1.0)";
-  } else if (n == 2) {
-    os << "    const R " << U << " = " << L_(0, 0) << " * " << L_(1, 1) << " - " << L_(0, 1) << " * " << L_(0, 1) << ";\n";
-    adj[0][0] = L_(1, 1); adj[1][1] = L_(0, 0);
-    adj[0][1] = adj[1][0] = lam[0][1].empty() ? "R(0.0)" : "(-" + L_(0, 1) + ")";
-  } else if (n == 3) {
-    auto cof = [&](int r, int c) {
-      int r1 = (r + 1) % 3, r2 = (r + 2) % 3, c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-      return "(" + L_(r1, c1) + " * " + L_(r2, c2) + " - " + L_(r1, c2) + " * " + L_(r2, c1) + ")";
-    };
-    for (int r = 0; r < 3; ++r) for (int c = r; c < 3; ++c) {
-      std::string v = P + "_A" + std::to_string(r) + std::to_string(c);
-      os << "    const R " << v << " = " << cof(c, r) << ";\n";
-      adj[r][c] = adj[c][r] = v;
-    }
-    os << "    const R " << U << " = " << L_(0, 0) << " * " << adj[0][0] << " + " << L_(0, 1) << " * " << adj[1][0]
-       << " + " << L_(0, 2) << " * " << adj[2][0] << ";\n";
-  } else {
-    fprintf(stderr, "loop order %d not supported by the emitter\n", n);
-    exit(1);
-  }
+  os << "    const R " << U << " = " << Up.horner() << ";\n";
   os << "    const R " << P << "_iU = R(1.0) / " << U << ";\n";
-  // J vectors and Q coefficients for every line with a non-zero coefficient
-  auto emitJ = [&](const std::vector<double> &coef, const char *tag) -> std::vector<std::string> {
-    std::vector<std::string> J(n);
-    for (int a = 0; a < n; ++a) {
-      std::string s;
-      for (int l = 0; l < L; ++l)
-        if (T.eta[l][a] && coef[l] != 0.0) {
-          std::string term = (coef[l] == 1.0 ? "" : "R(" + dstr(coef[l]) + ") * ") + "z[" + std::to_string(l) + "]";
-          s += s.empty() ? term : " + " + term;
-        }
-      if (s.empty()) { J[a] = ""; continue; }
-      J[a] = P + "_J" + tag + std::to_string(a);
-      os << "    const R " << J[a] << " = " << s << ";\n";
-    }
+  auto Jpoly = [&](const std::vector<double> &coef) {
+    std::vector<Poly> J(n);
+    for (int a = 0; a < n; ++a)
+      for (int l = 0; l < L; ++l) if (T.eta[l][a] && coef[l] != 0.0) J[a] = J[a] + Poly::var(l) * coef[l];
     return J;
   };
-  // adj * J
-  auto emitAJ = [&](const std::vector<std::string> &J, const char *tag) -> std::vector<std::string> {
-    std::vector<std::string> X(n);
-    for (int a = 0; a < n; ++a) {
-      std::string s;
-      for (int b = 0; b < n; ++b) if (!J[b].empty() && !(adj[a][b] == "R(0.0)")) s += (s.empty() ? "" : " + ") + adj[a][b] + " * " + J[b];
-      if (s.empty()) continue;
-      X[a] = P + "_X" + tag + std::to_string(a);
-      os << "    const R " << X[a] << " = " << s << ";\n";
-    }
+  auto Xpoly = [&](const std::vector<Poly> &J) {
+    std::vector<Poly> X(n);
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b) X[a] = X[a] + adjp[a][b] * J[b];
     return X;
   };
-  auto coefQ = [&](const std::vector<double> &coef, const std::vector<std::string> &X, int l, const char *tag) -> std::string {
-    // Q coefficient of line l: coef_l - (eta_l . adj . J) / U
-    std::string s;
-    for (int a = 0; a < n; ++a) if (T.eta[l][a] && !X[a].empty()) s += (s.empty() ? "" : " + ") + X[a];
+  auto Jp = Jpoly(T.alpha), Jq = Jpoly(T.beta), Jk = Jpoly(T.kappa);
+  auto Xp = Xpoly(Jp), Xq = Xpoly(Jq), Xk = Xpoly(Jk);
+  std::vector<std::string> A(L), C(L), K(L);
+  // Q coefficient of line l times U: coef_l U - eta_l . adj . J
+  auto emitQ = [&](const std::vector<double> &coef, const std::vector<Poly> &X, int l, const char *tag) -> std::string {
+    Poly q = Up * coef[l];
+    for (int a = 0; a < n; ++a) if (T.eta[l][a]) q = q - X[a];
+    if (q.zero()) return "";
     std::string v = P + "_" + tag + std::to_string(l);
-    if (s.empty()) { os << "    const R " << v << " = R(" << dstr(coef[l]) << ");\n"; return v; }
-    os << "    const R " << v << " = R(" << dstr(coef[l]) << ") - (" << s << ") * " << P << "_iU;\n";
+    os << "    const R " << v << " = (" << q.horner() << ") * " << P << "_iU;\n";
     return v;
   };
-  auto Jp = emitJ(T.alpha, "p"), Jq = emitJ(T.beta, "q"), Jk = emitJ(T.kappa, "k");
-  auto Xp = emitAJ(Jp, "p"), Xq = emitAJ(Jq, "q"), Xk = emitAJ(Jk, "k");
-  bool anyp = false, anyq = false, anyk = false;
-  for (int l = 0; l < L; ++l) { anyp |= T.alpha[l] != 0; anyq |= T.beta[l] != 0; anyk |= T.kappa[l] != 0; }
-  std::vector<std::string> A(L), C(L), K(L);
-  // V = sum_e z - sum_l z_l A_l^2
+  for (int l = 0; l < g.n_elec(); ++l) {
+    A[l] = emitQ(T.alpha, Xp, l, "Ap");
+    C[l] = emitQ(T.beta, Xq, l, "Cq");
+    K[l] = emitQ(T.kappa, Xk, l, "Kk");
+  }
+  // V = sum_{electrons without external momentum} z + Jp . adj . Jp / U
   std::string V = P + "_V";
   {
-    std::string s;
-    for (int l = 0; l < g.n_elec(); ++l) s += (s.empty() ? "" : " + ") + std::string("z[") + std::to_string(l) + "]";
-    os << "    R " << V << " = " << s << ";\n";
-    if (anyp)
-      for (int l = 0; l < L; ++l) {
-        bool need = T.alpha[l] != 0.0;
-        for (int a = 0; a < n; ++a) if (T.eta[l][a] && !Xp[a].empty()) need = true;
-        if (!need) continue;
-        A[l] = coefQ(T.alpha, Xp, l, "Ap");
-        os << "    " << V << " = " << V << " - z[" << l << "] * " << A[l] << " * " << A[l] << ";\n";
-      }
-  }
-  if (anyq) for (int l = 0; l < g.n_elec(); ++l) {
-    bool need = T.beta[l] != 0.0;
-    for (int a = 0; a < n; ++a) if (T.eta[l][a] && !Xq[a].empty()) need = true;
-    if (need) C[l] = coefQ(T.beta, Xq, l, "Cq");
-  }
-  if (anyk) for (int l = 0; l < g.n_elec(); ++l) {
-    bool need = T.kappa[l] != 0.0;
-    for (int a = 0; a < n; ++a) if (T.eta[l][a] && !Xk[a].empty()) need = true;
-    if (need) K[l] = coefQ(T.kappa, Xk, l, "Kk");
+    Poly uv;
+    for (int l = 0; l < g.n_elec(); ++l) if (T.alpha[l] == 0.0) uv = uv + Up * Poly::var(l);
+    for (int a = 0; a < n; ++a) uv = uv + Jp[a] * Xp[a];
+    os << "    const R " << V << " = (" << uv.horner() << ") * " << P << "_iU;\n";
   }
   // B_ij on demand
   std::map<std::pair<int, int>, std::string> Bc;
@@ -572,11 +604,11 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
     auto key = std::make_pair(i, j);
     auto it = Bc.find(key);
     if (it != Bc.end()) return it->second;
-    std::string s;
+    Poly bp;
     for (int a = 0; a < n; ++a) for (int b = 0; b < n; ++b)
-      if (T.eta[i][a] && T.eta[j][b] && adj[a][b] != "R(0.0)") s += (s.empty() ? "" : " + ") + adj[a][b];
-    std::string v = s.empty() ? "" : P + "_B" + std::to_string(i) + "_" + std::to_string(j);
-    if (!s.empty()) os << "    const R " << v << " = " << s << ";\n";
+      if (T.eta[i][a] && T.eta[j][b]) bp = bp + adjp[a][b];
+    std::string v = bp.zero() ? "" : P + "_B" + std::to_string(i) + "_" + std::to_string(j);
+    if (!bp.zero()) os << "    const R " << v << " = " << bp.horner() << ";\n";
     Bc[key] = v;
     return v;
   };
