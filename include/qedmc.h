@@ -97,9 +97,11 @@ int qed_ctx_set_stream(qed_ctx *ctx, uintptr_t stream);
  * the summation order only. */
 int qed_ctx_set_launch(qed_ctx *ctx, int threads_per_block, int blocks);
 /* Relative rounding-error threshold above which a point is re-evaluated in
- * double-double (Sec. 3: arithmetics of different precisions).  Default 1e-12.
- * The estimate is 16 ulp x (sum of the absolute values of the integrand's
- * monomials) / |f|. */
+ * double-double (Sec. 3: arithmetics of different precisions).  Default 1e-8
+ * (per-point errors far below the statistical error of any run); 1e-12 makes
+ * every accepted FP64 value accurate to 1e-12.  The estimate is
+ * 8 ulp x (sum of the absolute values of the integrand's monomials) / |f|; the
+ * double-double result is accepted under the same rule with its own ulp. */
 int qed_ctx_set_threshold(qed_ctx *ctx, double rel_err);
 const char *qed_last_error(void);
 

@@ -127,7 +127,7 @@ _LET = _string.ascii_letters
 _PAIR_LABELS = "abdefghiklmnopqtuvwxyABCDEFGHIKLOPQRSTUVWXY"
 
 
-def _chain(items, pairs, out_free, Bn=1):
+def _chain(items, pairs, out_free, Bn=1, ctype=complex):
     """Product items[-1] ... items[0] of 4x4 factors, built right to left.
 
     items: list of (array, has_batch, free) where array is [B,4,4] (batch),
@@ -143,7 +143,7 @@ def _chain(items, pairs, out_free, Bn=1):
         partner[j] = i
     # R dims: [B, open axes..., 4, 4]; open axes are free indices or the
     # alpha of a pair whose second gamma is still to come.
-    R = np.broadcast_to(np.eye(4, dtype=complex), (Bn, 4, 4)).copy()
+    R = np.broadcast_to(np.eye(4, dtype=ctype), (Bn, 4, 4)).copy()
     names = []
 
     def lmul(M, R, nb):
@@ -271,14 +271,18 @@ class TermEvaluator:
         return seq
 
     # ---- evaluate ---------------------------------------------------------
-    def __call__(self, z):
-        z = np.atleast_2d(np.asarray(z, dtype=np.float64))
-        P = polynomials(z, self.eta, self.alpha, self.beta, self.kappa, self.mass2)
+    def __call__(self, z, dtype=np.float64):
+        """dtype np.float64, or np.longdouble for the extended-precision
+        reference used to check re-evaluated (flagged) points."""
+        self.dtype = dtype
+        self.ctype = complex if dtype == np.float64 else np.clongdouble
+        z = np.atleast_2d(np.asarray(z, dtype=dtype))
+        P = polynomials(z, self.eta, self.alpha, self.beta, self.kappa, self.mass2, dtype=dtype)
         self.P = P
         U, V = P["U"], P["V"]
         n = self.g.n
         val = self._block_value(self.root, z)
-        total = np.zeros(z.shape[0])
+        total = np.zeros(z.shape[0], dtype=dtype)
         for k in range(0, n):
             if k >= len(val):
                 break
@@ -290,7 +294,7 @@ class TermEvaluator:
         """(A pslash + 1) (or (A pslash - 1)) with the q / k parts handled by
         the derivative pass; returns [B,4,4]."""
         B = A.shape[0]
-        m = np.zeros((B, 4, 4), dtype=complex)
+        m = np.zeros((B, 4, 4), dtype=self.ctype)
         s = -1.0 if minus_mass else 1.0
         m[:, 0, 0] = m[:, 1, 1] = s + A
         m[:, 2, 2] = m[:, 3, 3] = s - A
@@ -329,7 +333,7 @@ class TermEvaluator:
         mom_idx = list(range(len(mom)))
         for pat in _pairings(mom_idx):
             k = len(pat)
-            coef = np.ones(Bn)
+            coef = np.ones(Bn, dtype=self.dtype)
             for (i, j) in pat:
                 coef = coef * b_matrix(P["adj"], mom[i][1], mom[j][1])
             if np.all(coef == 0.0):
@@ -342,9 +346,9 @@ class TermEvaluator:
             r = self._project(bl, seq, mom, contracted, pairs, Bn)
             own[k] = own.get(k, 0.0) + coef * r
         kmax = max(own.keys()) if own else 0
-        vals = [own.get(k, np.zeros(Bn)) for k in range(kmax + 1)]
+        vals = [own.get(k, np.zeros(Bn, dtype=self.dtype)) for k in range(kmax + 1)]
         for cv in child_vals:
-            new = [np.zeros(Bn) for _ in range(len(vals) + len(cv) - 1)]
+            new = [np.zeros(Bn, dtype=self.dtype) for _ in range(len(vals) + len(cv) - 1)]
             for i, x in enumerate(vals):
                 for j, y in enumerate(cv):
                     new[i + j] = new[i + j] + x * y
@@ -386,26 +390,26 @@ class TermEvaluator:
             for k, o in seq)
         if bl.proj in ("F2", "L", "UV"):
             assert has_mu
-            G = _chain(self._items(bl, seq, mom, contracted, Bn), pairs, ["M"], Bn)
+            G = _chain(self._items(bl, seq, mom, contracted, Bn), pairs, ["M"], Bn, self.ctype)
             if bl.proj == "L":
                 return np.real(dirac.l_of_vertex(G))
             if bl.proj == "UV":
                 return np.real(dirac.gamma_mu_coeff(G))
-            H = np.zeros((Bn, 4, 3, 4, 4), dtype=complex)
+            H = np.zeros((Bn, 4, 3, 4, 4), dtype=self.ctype)
             for (t, eta, A, C, K, minus) in mom:
                 if t in contracted or np.all(C == 0.0):
                     continue
-                H = H + _chain(self._items(bl, seq, mom, contracted, Bn, (t, "q")), pairs, ["M", "J"], Bn)
+                H = H + _chain(self._items(bl, seq, mom, contracted, Bn, (t, "q")), pairs, ["M", "J"], Bn, self.ctype)
             return np.real(dirac.f2_of_vertex(G, H))
         if bl.proj == "SEmass":
-            S = _chain(self._items(bl, seq, mom, contracted, Bn), pairs, [], Bn)
+            S = _chain(self._items(bl, seq, mom, contracted, Bn), pairs, [], Bn, self.ctype)
             return np.real(0.5 * np.trace(S[:, 0:2, 0:2], axis1=-2, axis2=-1))
         if bl.proj == "SEwf":
-            D = np.zeros((Bn, 4, 4, 4), dtype=complex)
+            D = np.zeros((Bn, 4, 4, 4), dtype=self.ctype)
             for (t, eta, A, C, K, minus) in mom:
                 if t in contracted or np.all(K == 0.0):
                     continue
-                D = D + _chain(self._items(bl, seq, mom, contracted, Bn, (t, "k")), pairs, ["N"], Bn)
+                D = D + _chain(self._items(bl, seq, mom, contracted, Bn, (t, "k")), pairs, ["N"], Bn, self.ctype)
             # D[nu] = dSigma/dk^nu = b gamma_nu (lower index): tr(gamma^nu D_nu) = 16 b
             acc = 0.0
             for nu in range(4):
@@ -468,9 +472,9 @@ class Integrand:
         else:
             self.terms = [(1, TermEvaluator(g, "q", "F2", []), ((), "q", "F2"))]
 
-    def __call__(self, z, return_terms=False):
-        z = np.atleast_2d(np.asarray(z, dtype=np.float64))
-        vals = [s * ev(z) for s, ev, _ in self.terms]
+    def __call__(self, z, return_terms=False, dtype=np.float64):
+        z = np.atleast_2d(np.asarray(z, dtype=dtype))
+        vals = [s * ev(z, dtype=dtype) for s, ev, _ in self.terms]
         tot = np.sum(vals, axis=0)
         if return_terms:
             return tot, vals

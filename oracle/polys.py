@@ -20,29 +20,59 @@ from __future__ import annotations
 import numpy as np
 
 
-def polynomials(z, eta, alpha, beta, kappa, mass2):
+def _det_adj_cofactor(lam):
+    """Determinant and adjugate by cofactor expansion (any float dtype,
+    n <= 3); used for the extended-precision mode."""
+    B, n, _ = lam.shape
+    if n == 1:
+        return lam[:, 0, 0].copy(), np.ones_like(lam)
+    if n == 2:
+        adj = np.empty_like(lam)
+        adj[:, 0, 0] = lam[:, 1, 1]
+        adj[:, 1, 1] = lam[:, 0, 0]
+        adj[:, 0, 1] = -lam[:, 0, 1]
+        adj[:, 1, 0] = -lam[:, 1, 0]
+        return lam[:, 0, 0] * lam[:, 1, 1] - lam[:, 0, 1] * lam[:, 1, 0], adj
+    if n == 3:
+        adj = np.empty_like(lam)
+        for r in range(3):
+            for c in range(3):
+                rr = [i for i in range(3) if i != c]
+                cc = [j for j in range(3) if j != r]
+                m = lam[:, rr][:, :, cc]
+                adj[:, r, c] = (-1) ** (r + c) * (m[:, 0, 0] * m[:, 1, 1] - m[:, 0, 1] * m[:, 1, 0])
+        det = lam[:, 0, 0] * adj[:, 0, 0] + lam[:, 0, 1] * adj[:, 1, 0] + lam[:, 0, 2] * adj[:, 2, 0]
+        return det, adj
+    raise ValueError("extended precision supports n <= 3")
+
+
+def polynomials(z, eta, alpha, beta, kappa, mass2, dtype=np.float64):
     """z: [B, L]; eta: [L, n] (0/1 incidence); alpha/beta/kappa/mass2: [L].
+    dtype: np.float64 (default) or np.longdouble (64-bit mantissa on x86).
 
     Returns dict with U [B], adj [B,n,n], A, C, K [B, L], V [B].
     """
-    z = np.atleast_2d(np.asarray(z, dtype=np.float64))
-    eta = np.asarray(eta, dtype=np.float64)
+    z = np.atleast_2d(np.asarray(z, dtype=dtype))
+    eta = np.asarray(eta, dtype=dtype)
     n = eta.shape[1]
     lam = np.einsum("bl,la,lc->bac", z, eta, eta)
     if n == 0:
-        U = np.ones(z.shape[0])
-        inv = np.zeros((z.shape[0], 0, 0))
-    else:
+        U = np.ones(z.shape[0], dtype=dtype)
+        inv = np.zeros((z.shape[0], 0, 0), dtype=dtype)
+    elif dtype == np.float64:
         U = np.linalg.det(lam)
         inv = np.linalg.inv(lam)
+    else:
+        U, adj0 = _det_adj_cofactor(lam)
+        inv = adj0 / U[:, None, None]
     adj = inv * U[:, None, None]
     out = {"U": U, "adj": adj, "inv": inv}
     for name, coef in (("A", alpha), ("C", beta), ("K", kappa)):
-        coef = np.asarray(coef, dtype=np.float64)
+        coef = np.asarray(coef, dtype=dtype)
         J = np.einsum("bl,la,l->ba", z, eta, coef)
         shift = np.einsum("la,bac,bc->bl", eta, inv, J)
         out[name] = coef[None, :] - shift
-    out["V"] = z @ np.asarray(mass2, dtype=np.float64) - np.sum(z * out["A"] ** 2, axis=1)
+    out["V"] = z @ np.asarray(mass2, dtype=dtype) - np.sum(z * out["A"] ** 2, axis=1)
     return out
 
 

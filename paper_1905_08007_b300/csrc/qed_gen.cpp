@@ -399,10 +399,21 @@ struct DFS {
       case IT_LINE:
       case IT_INS: {
         int f = slot_of_item[t];
-        Mono one = mono_identity();
-        if (I.kind == IT_INS) for (int r = 0; r < 4; ++r) one.val[r] = -1.0;
-        push(one, mu, dj, pm, dv);
-        if (allow_p) push(GAM[0], mu, dj, pm | (1u << f), dv);
+        const double sgn = (I.kind == IT_INS) ? -1.0 : 1.0;
+        if (allow_p) {
+          // (A pslash + 1) = (1+A) P+ + (1-A) P-;  (A pslash - 1) = -(1-A) P+ - (1+A) P-
+          // bit 2f: factor (1 + A_f), bit 2f+1: factor (1 - A_f)
+          Mono pp, pmn;
+          for (int r = 0; r < 4; ++r) { pp.col[r] = r; pmn.col[r] = r; pp.val[r] = r < 2 ? sgn : 0.0; pmn.val[r] = r < 2 ? 0.0 : sgn; }
+          const uint32_t bp = (I.kind == IT_INS) ? (1u << (2 * f + 1)) : (1u << (2 * f));
+          const uint32_t bm = (I.kind == IT_INS) ? (1u << (2 * f)) : (1u << (2 * f + 1));
+          push(pp, mu, dj, pm | bp, dv);
+          push(pmn, mu, dj, pm | bm, dv);
+        } else {
+          Mono one = mono_identity();
+          for (int r = 0; r < 4; ++r) one.val[r] = sgn;
+          push(one, mu, dj, pm, dv);
+        }
         if (dv < 0 && allow_q)
           for (int j = 1; j < 4; ++j) { Mono m = GAM[j]; for (int r = 0; r < 4; ++r) m.val[r] = -m.val[r]; push(m, mu, j, pm, f); }
         if (dv < 0 && allow_k)
@@ -585,7 +596,6 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
     return v;
   };
   for (int l = 0; l < g.n_elec(); ++l) {
-    A[l] = emitQ(T.alpha, Xp, l, "Ap");
     C[l] = emitQ(T.beta, Xq, l, "Cq");
     K[l] = emitQ(T.kappa, Xk, l, "Kk");
   }
@@ -597,6 +607,20 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
     for (int a = 0; a < n; ++a) uv = uv + Jp[a] * Xp[a];
     os << "    const R " << V << " = (" << uv.horner() << ") * " << P << "_iU;\n";
   }
+  // (1 + A_l) and (1 - A_l), expanded symbolically: (U +- U A_l) / U
+  std::map<std::pair<int, int>, std::string> onepm_cache;
+  auto onepm = [&](int l, int minus) -> std::string {
+    auto key = std::make_pair(l, minus);
+    auto it = onepm_cache.find(key);
+    if (it != onepm_cache.end()) return it->second;
+    Poly q = Up * T.alpha[l];
+    for (int a = 0; a < n; ++a) if (T.eta[l][a]) q = q - Xp[a];
+    Poly w = minus ? Up - q : Up + q;
+    std::string v = P + (minus ? "_Bm" : "_Bp") + std::to_string(l);
+    os << "    const R " << v << " = (" << w.horner() << ") * " << P << "_iU;\n";
+    onepm_cache[key] = v;
+    return v;
+  };
   // B_ij on demand
   std::map<std::pair<int, int>, std::string> Bc;
   auto Bij = [&](int i, int j) -> std::string {
@@ -695,13 +719,13 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
         double cr = snap(c.real());
         if (cr == 0.0) continue;
         std::string mono, amono;
-        for (int f = 0; f < m; ++f) if (kv.first.pmask >> f & 1) {
-          const std::string &v = A[mom_line[f]];
-          if (v.empty()) { mono = "ZERO"; break; }
-          mono += " * " + v;
-          amono += " * " + fabsvar(v);
-        }
-        if (mono == "ZERO") continue;
+        for (int f = 0; f < m; ++f)
+          for (int pmn = 0; pmn < 2; ++pmn)
+            if (kv.first.pmask >> (2 * f + pmn) & 1) {
+              const std::string v = onepm(mom_line[f], pmn);
+              mono += " * " + v;
+              amono += " * " + fabsvar(v);
+            }
         if (kv.first.deriv >= 0) {
           int f = kv.first.deriv;
           const std::string &v = (B.proj == PR_F2) ? C[mom_line[f]] : K[mom_line[f]];

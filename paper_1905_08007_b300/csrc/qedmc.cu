@@ -58,7 +58,7 @@ struct qed_ctx {
   int threads = 256;
   int blocks = 0;            // 0 = 4 x SMs
   int sms = 148;
-  double thresh = 1e-12;
+  double thresh = 1e-8;
   // scratch owned by the context
   double *partials = nullptr;
   unsigned long long *counts = nullptr;

