@@ -73,14 +73,21 @@ def test_points_density_integrand_match_oracle(ctx, n, gi, begin, count):
     # subsample: accepted FP64 values and double-double values of flagged
     # points, both to 1e-12 relative
     sub = np.arange(0, count, 5)
-    fl_ld = Integrand(og)(z[sub], dtype=np.longdouble).astype(np.float64)
+    fld = Integrand(og)(z[sub], dtype=np.longdouble)
+    # the oracle's own rounding: its long-double value is 2^11 times finer
+    # than its FP64 value, so the FP64-long-double gap / 2^11 estimates the
+    # long-double error (x8 margin); it matters only at the IR corners where
+    # the oracle's V = sum z - sum z A^2 cancels
+    ref_err = 8.0 * 2.0 ** -11 * np.abs(fo[sub] - fld.astype(np.float64))
+    fl_ld = fld.astype(np.float64)
+    tol = 1e-12 * np.abs(fl_ld) + ref_err
     zt = torch.tensor(z[sub], dtype=torch.float64, device="cuda")
     fdd = d.eval_points(zt, prec=1).cpu().numpy()
     oks = ok[sub]
-    rel64 = np.abs(f[sub][oks] - fl_ld[oks]) / np.abs(fl_ld[oks])
-    reldd = np.abs(fdd - fl_ld) / np.abs(fl_ld)
-    assert rel64.max(initial=0.0) < 1e-12, rel64.max()
-    assert np.quantile(reldd, 0.99) < 1e-12, np.sort(reldd)[-5:]
+    bad64 = np.abs(f[sub] - fl_ld) > tol
+    baddd = np.abs(fdd - fl_ld) > tol
+    assert not np.any(bad64 & oks), (np.abs(f[sub] - fl_ld) / np.abs(fl_ld))[bad64 & oks]
+    assert baddd.mean() < 0.01, (np.abs(fdd - fl_ld) / np.abs(fl_ld))[baddd]
 
 
 @pytest.mark.parametrize("n,gi", GRAPHS)
@@ -95,8 +102,12 @@ def test_double_double_agrees_with_fp64_and_oracle(ctx, n, gi):
     np.testing.assert_allclose(f64[ok], f.cpu().numpy()[ok], rtol=1e-12)
     np.testing.assert_allclose(f64[ok], fdd[ok], rtol=1e-12)
     sub = np.arange(0, 512, 8)
-    fo = Integrand(o_enum(n)[gi])(z.cpu().numpy()[sub], dtype=np.longdouble).astype(np.float64)
-    np.testing.assert_allclose(fdd[sub][ok[sub]], fo[ok[sub]], rtol=1e-12)
+    og = o_enum(n)[gi]
+    zz = z.cpu().numpy()[sub]
+    fld = Integrand(og)(zz, dtype=np.longdouble)
+    f64o = Integrand(og)(zz)
+    tol = 1e-12 * np.abs(fld.astype(np.float64)) + 8.0 * 2.0 ** -11 * np.abs(f64o - fld.astype(np.float64))
+    assert np.all(np.abs(fdd[sub] - fld.astype(np.float64)) <= tol)
 
 
 def test_one_loop_estimate_is_one_half(ctx):
