@@ -141,6 +141,28 @@ int qed_dump_points(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed,
  * (prec = 0) or double-double (prec = 1, result rounded to double). */
 int qed_eval_points(qed_diag *d, const double *z_dev, uint64_t n, int prec, double *f_dev);
 
+/* ---- batched integration of a graph set --------------------------------- */
+/* Options of qed_integrate_batch.  Zero-initialised fields take defaults. */
+typedef struct {
+  int policy;          /* 0 = variance-driven (Neyman: N_g ~ sigma_g / sqrt(cost_g)), 1 = equal */
+  int rounds;          /* allocation rounds (default 4); round 0 is equal */
+  uint64_t chunk;      /* samples per work item (default 262144, <= 2^31) */
+  int use_graph;       /* 0 = default: capture one round as a CUDA graph and replay it; -1 = plain launches */
+  int list_div;        /* flagged-list capacity per item = chunk / list_div (default 16) */
+} qed_batch_opts;
+
+/* Integrate the k graphs d[0..k-1] (all loaded on the same context) with
+ * total_samples samples in all, in one persistent launch per round: blocks
+ * take (graph, counter-block) work items from a device queue, so graphs of
+ * different cost share the GPU.  After round r the samples of round r+1 are
+ * split by the running per-sample variance and the cost model (FP64 ops per
+ * sample, qed_diagram_flops, weighted by the flagged fraction).  Every graph's
+ * samples are consecutive counters from 0, so a result depends only on
+ * (seed, graphs, total, options).  out_k[g] receives graph g's result
+ * (seconds and launches of the whole call on every entry). */
+int qed_integrate_batch(qed_ctx *ctx, qed_diag *const *d, int k, uint64_t total_samples, uint64_t seed,
+                        const qed_batch_opts *opts, qed_result *out_k);
+
 /* Merge replica results over disjoint sample ranges: the raw moments add in
  * double-double, so the merge is exact and order-fixed: out = a (+) b. */
 int qed_result_merge(const qed_result *a, const qed_result *b, qed_result *out);

@@ -36,6 +36,11 @@ class _Pdf(C.Structure):
     _fields_ = [("deg", C.POINTER(C.c_double)), ("c_div", C.c_double), ("d_min", C.c_double)]
 
 
+class _BatchOpts(C.Structure):
+    _fields_ = [("policy", C.c_int), ("rounds", C.c_int), ("chunk", C.c_uint64), ("use_graph", C.c_int),
+                ("list_div", C.c_int)]
+
+
 class _Result(C.Structure):
     _fields_ = [("value", C.c_double), ("variance", C.c_double), ("sum_w", C.c_double * 2),
                 ("sum_w2", C.c_double * 2), ("n", C.c_uint64), ("n_flagged", C.c_uint64),
@@ -136,6 +141,8 @@ def load_library():
         "qed_eval_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_void_p]),
         "qed_result_merge": (C.c_int, [P(_Result), P(_Result), P(_Result)]),
         "qed_diagram_flops": (C.c_int, [C.c_void_p, P(C.c_double)]),
+        "qed_integrate_batch": (C.c_int, [C.c_void_p, P(C.c_void_p), C.c_int, C.c_uint64, C.c_uint64,
+                                          P(_BatchOpts), P(_Result)]),
         "qed_fp64_peak": (C.c_int, [C.c_int, C.c_double, P(C.c_double)]),
     }
     for name, (res, args) in sig.items():
@@ -208,6 +215,17 @@ class Context:
 
     def load(self, g: Graph, deg=None, c_div: float = 0.0, d_min: float = 0.0) -> "Diagram":
         return Diagram(self, g, deg, c_div, d_min)
+
+    def integrate_batch(self, diagrams, total_samples: int, seed: int = 0, policy: str = "variance",
+                        rounds: int = 4, chunk: int = 1 << 18, use_graph: bool = True, list_div: int = 16):
+        """qed_integrate_batch: all graphs in one persistent launch per round,
+        samples shared by running variance (policy "variance") or equally."""
+        k = len(diagrams)
+        arr = (C.c_void_p * k)(*[d._h.value for d in diagrams])
+        o = _BatchOpts(0 if policy == "variance" else 1, rounds, chunk, 0 if use_graph else -1, list_div)
+        out = (_Result * k)()
+        _check(load_library().qed_integrate_batch(self._h, arr, k, int(total_samples), seed, C.byref(o), out))
+        return [Result._from_c(out[i]) for i in range(k)]
 
     def close(self):
         if self._h:

@@ -57,7 +57,7 @@ def build(orders=DEFAULT_ORDERS, force=False, verbose_ptxas=False, jobs=None):
     BUILD.mkdir(exist_ok=True)
     GEN.mkdir(exist_ok=True)
     gen_src = [CSRC / "qed_gen.cpp", CSRC / "qed_graph.hpp"]
-    lib_src = [CSRC / "qedmc.cu", CSRC / "qed_kernels.cuh", CSRC / "qed_dd.cuh",
+    lib_src = [CSRC / "qedmc.cu", CSRC / "qed_kernels.cuh", CSRC / "qed_batch.cuh", CSRC / "qed_dd.cuh",
                CSRC / "qed_graph.hpp", INCLUDE / "qedmc.h"]
     stamp = BUILD / "libqedmc.stamp"
     key = _digest(gen_src + lib_src, extra=repr(orders) + ARCH + repr(verbose_ptxas))
@@ -83,6 +83,18 @@ def build(orders=DEFAULT_ORDERS, force=False, verbose_ptxas=False, jobs=None):
         tu = GEN / f"k_{gid}.cu"
         tu.write_text(f'#include "qed_kernels.cuh"\n#include "g_{gid}.cuh"\nQED_DEFINE_KSET({gid}, {lines})\n')
         units.append((tu, objdir / f"k_{gid}.o"))
+    # the persistent batched kernels: one switch over every generated graph
+    btu = GEN / "k_batch.cu"
+    inc = "".join(f'#include "g_{gid}.cuh"\n' for gid, _ in ids)
+    c64 = " ".join(f"case {gid}: batch_item_fp64<{gid}, {ln}>(B, it, I, smem); break;" for gid, ln in ids)
+    cdd = " ".join(f"case {gid}: batch_item_dd<{gid}, {ln}>(B, it, I, smem); break;" for gid, ln in ids)
+    btu.write_text(
+        f'#define QED_BATCH_TU 1\n#include "qed_batch.cuh"\n{inc}'
+        f'__device__ void batch_dispatch_fp64(const BatchParams &B, unsigned int it, const BatchItem &I, double *smem) {{\n'
+        f'  switch (B.diags[I.diag].fid) {{ {c64} default: break; }}\n}}\n'
+        f'__device__ void batch_dispatch_dd(const BatchParams &B, unsigned int it, const BatchItem &I, double *smem) {{\n'
+        f'  switch (B.diags[I.diag].fid) {{ {cdd} default: break; }}\n}}\n')
+    units.append((btu, objdir / "k_batch.o"))
     units.append((CSRC / "qedmc.cu", objdir / "qedmc.o"))
 
     def compile_one(u):

@@ -142,9 +142,11 @@ struct KSum {
   }
 };
 
-// Reduce (hi, lo) pairs of a block into partials[blockIdx.x]
+// Reduce (hi, lo) pairs of a block into partials[slot] (slot = blockIdx.x
+// for the per-graph kernels, the work-item index for the batched kernels).
 __device__ __forceinline__ void block_reduce_store(KSum a, KSum b, unsigned long long nf, unsigned long long nu,
-                                                   double *partials, unsigned long long *counts) {
+                                                   double *partials, unsigned long long *counts,
+                                                   unsigned int slot) {
   dd x = dd_from_sum(a.s, a.c), y = dd_from_sum(b.s, b.c);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -169,11 +171,12 @@ __device__ __forceinline__ void block_reduce_store(KSum a, KSum b, unsigned long
       F += redc[w][0];
       Un += redc[w][1];
     }
-    double *p = partials + 4 * blockIdx.x;
+    double *p = partials + 4 * size_t(slot);
     p[0] = X.hi; p[1] = X.lo; p[2] = Y.hi; p[3] = Y.lo;
-    counts[2 * blockIdx.x] = F;
-    counts[2 * blockIdx.x + 1] = Un;
+    counts[2 * size_t(slot)] = F;
+    counts[2 * size_t(slot) + 1] = Un;
   }
+  __syncthreads();   // red[] is reused by the next call in persistent loops
 }
 
 // Main FP64 kernel: grid-stride over samples [begin, begin + n).
@@ -202,7 +205,7 @@ __global__ void __launch_bounds__(256) k_integrate(KParams P) {
       sw2.add(w * w);
     }
   }
-  block_reduce_store(sw, sw2, nflag, 0ull, P.partials, P.counts);
+  block_reduce_store(sw, sw2, nflag, 0ull, P.partials, P.counts, blockIdx.x);
 }
 
 // Double-double re-evaluation of flagged samples.  mode 0: the queue holds
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(256) k_redo_dd(KParams P, int mode, unsigned i
     sw.add(w);
     sw2.add(w * w);
   }
-  block_reduce_store(sw, sw2, 0ull, nunst, P.partials, P.counts);
+  block_reduce_store(sw, sw2, 0ull, nunst, P.partials, P.counts, blockIdx.x);
 }
 
 template <int FID, int N>

@@ -26,6 +26,7 @@
 #include "qedmc.h"
 #include "qed_graph.hpp"
 #include "qed_kernels.cuh"
+#include "qed_batch.cuh"
 #include "qed_registry.h"
 
 // ---------------------------------------------------------------------------
@@ -48,6 +49,8 @@ extern "C" const char *qed_last_error(void) { return g_err.c_str(); }
 QED_GENERATED_LIST(QED_DECL_KSET)
 #define QED_REF_KSET(id, lines) &qed_kset_##id,
 static const KernelSet *const g_kernels[] = {QED_GENERATED_LIST(QED_REF_KSET)};
+// persistent batched kernels (defined in the generated batch translation unit)
+extern const void *const qed_batch_kernels[2];
 
 // ---------------------------------------------------------------------------
 // host objects
@@ -480,5 +483,177 @@ extern "C" int qed_fp64_peak(int device, double ms, double *flops) {
   cudaEventDestroy(e1);
   cudaFree(out);
   *flops = best;
+  return QED_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched integration of a graph set (persistent kernel, variance-driven
+// allocation, one CUDA graph per round shape replayed every round)
+// ---------------------------------------------------------------------------
+namespace {
+struct DevBuf {
+  void *p = nullptr;
+  ~DevBuf() { if (p) cudaFree(p); }
+};
+struct HostBuf {
+  void *p = nullptr;
+  ~HostBuf() { if (p) cudaFreeHost(p); }
+};
+}  // namespace
+
+extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64_t total, uint64_t seed,
+                                   const qed_batch_opts *opts, qed_result *out) {
+  if (!c || !d || !out || k < 1) return set_err(QED_EINVAL, "bad arguments");
+  for (int g = 0; g < k; ++g)
+    if (!d[g] || d[g]->ctx != c) return set_err(QED_EINVAL, "every graph must be loaded on this context");
+  qed_batch_opts o;
+  std::memset(&o, 0, sizeof o);
+  if (opts) o = *opts;
+  const int rounds = o.rounds > 0 ? o.rounds : 4;
+  const uint64_t chunk = o.chunk > 0 ? o.chunk : (uint64_t(1) << 18);
+  const int list_div = o.list_div > 0 ? o.list_div : 16;
+  if (chunk > (uint64_t(1) << 31)) return set_err(QED_EINVAL, "chunk must be <= 2^31");
+  if (o.policy != 0 && o.policy != 1) return set_err(QED_EINVAL, "policy must be 0 or 1");
+  CUDA_TRY(cudaSetDevice(c->device));
+  // items per round (all rounds the same size so one captured graph serves all)
+  const uint64_t per_round = (total + rounds - 1) / rounds;
+  const unsigned int n_items = unsigned(std::max<uint64_t>(uint64_t(k), (per_round + chunk - 1) / chunk));
+  const uint32_t list_cap = uint32_t(std::max<uint64_t>(1, chunk / list_div));
+  int Nmax = 0;
+  for (int g = 0; g < k; ++g) Nmax = std::max(Nmax, d[g]->N);
+  const size_t smem = 3 * (size_t(1) << Nmax) * sizeof(double);
+  // device and pinned buffers
+  DevBuf dd_diags, dd_items, dd_next, dd_part, dd_cnt, dd_lists, dd_pdd, dd_cdd;
+  HostBuf h_items, h_out;
+  CUDA_TRY(cudaMalloc(&dd_diags.p, sizeof(BatchDiag) * k));
+  CUDA_TRY(cudaMalloc(&dd_items.p, sizeof(BatchItem) * n_items));
+  CUDA_TRY(cudaMalloc(&dd_next.p, sizeof(unsigned int)));
+  CUDA_TRY(cudaMalloc(&dd_part.p, sizeof(double) * 4 * n_items));
+  CUDA_TRY(cudaMalloc(&dd_cnt.p, sizeof(unsigned long long) * 2 * n_items));
+  CUDA_TRY(cudaMalloc(&dd_pdd.p, sizeof(double) * 4 * n_items));
+  CUDA_TRY(cudaMalloc(&dd_cdd.p, sizeof(unsigned long long) * 2 * n_items));
+  CUDA_TRY(cudaMalloc(&dd_lists.p, sizeof(uint32_t) * size_t(list_cap) * n_items));
+  const size_t out_bytes = n_items * (8 * sizeof(double) + 4 * sizeof(unsigned long long));
+  CUDA_TRY(cudaMallocHost(&h_items.p, sizeof(BatchItem) * n_items));
+  CUDA_TRY(cudaMallocHost(&h_out.p, out_bytes));
+  std::vector<BatchDiag> hd(k);
+  for (int g = 0; g < k; ++g) {
+    const size_t M = size_t(1) << d[g]->N;
+    hd[g].F = d[g]->d_tab; hd[g].G = d[g]->d_tab + M; hd[g].inv = d[g]->d_tab + 2 * M;
+    hd[g].logZ = d[g]->logZ; hd[g].stream = d[g]->stream_id; hd[g].fid = d[g]->fid; hd[g].N = d[g]->N; hd[g].pad = 0;
+  }
+  CUDA_TRY(cudaMemcpy(dd_diags.p, hd.data(), sizeof(BatchDiag) * k, cudaMemcpyHostToDevice));
+  BatchParams B;
+  B.diags = (const BatchDiag *)dd_diags.p; B.items = (const BatchItem *)dd_items.p; B.n_items = n_items;
+  B.next_item = (unsigned int *)dd_next.p; B.key0 = uint32_t(seed); B.key1 = uint32_t(seed >> 32);
+  B.thresh = c->thresh; B.part = (double *)dd_part.p; B.cnt = (unsigned long long *)dd_cnt.p;
+  B.lists = (uint32_t *)dd_lists.p; B.list_cap = list_cap;
+  B.part_dd = (double *)dd_pdd.p; B.cnt_dd = (unsigned long long *)dd_cdd.p;
+  int occ = 0;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)qed_batch_kernels[0], 256, smem));
+  const int grid1 = std::max(1, occ) * c->sms;
+  const int grid2 = std::min<int>(int(n_items), 4 * c->sms);
+  // host-side layout of the pinned output block
+  double *o_part = (double *)h_out.p;
+  double *o_pdd = o_part + 4 * size_t(n_items);
+  unsigned long long *o_cnt = (unsigned long long *)(o_pdd + 4 * size_t(n_items));
+  unsigned long long *o_cdd = o_cnt + 2 * size_t(n_items);
+  auto enqueue_round = [&](cudaStream_t st) -> int {
+    CUDA_TRY(cudaMemcpyAsync(dd_items.p, h_items.p, sizeof(BatchItem) * n_items, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(dd_next.p, 0, sizeof(unsigned int), st));
+    void *args[] = {&B};
+    CUDA_TRY(cudaLaunchKernel(qed_batch_kernels[0], dim3(grid1), dim3(256), args, smem, st));
+    CUDA_TRY(cudaLaunchKernel(qed_batch_kernels[1], dim3(grid2), dim3(256), args, smem, st));
+    CUDA_TRY(cudaMemcpyAsync(o_part, dd_part.p, sizeof(double) * 4 * n_items, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(o_pdd, dd_pdd.p, sizeof(double) * 4 * n_items, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(o_cnt, dd_cnt.p, sizeof(unsigned long long) * 2 * n_items, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(o_cdd, dd_cdd.p, sizeof(unsigned long long) * 2 * n_items, cudaMemcpyDeviceToHost, st));
+    return QED_OK;
+  };
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t st = c->stream;
+  bool own_stream = false;
+  if (o.use_graph >= 0) {
+    if (st == 0) { CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own_stream = true; }
+    cudaGraph_t graph;
+    CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_round(st);
+    cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (rc) return rc;
+    if (ce != cudaSuccess) return set_err(QED_ECUDA, std::string("capture: ") + cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return set_err(QED_ECUDA, std::string("instantiate: ") + cudaGetErrorString(ce));
+  }
+  // per-graph running state
+  std::vector<qed_result> R(k);
+  std::vector<uint64_t> next(k, 0);
+  for (int g = 0; g < k; ++g) std::memset(&R[g], 0, sizeof(qed_result));
+  std::vector<double> weight(k, 1.0);
+  BatchItem *hi = (BatchItem *)h_items.p;
+  uint32_t launches = 0;
+  CUDA_TRY(cudaEventRecord(c->ev0, st));
+  for (int r = 0; r < rounds; ++r) {
+    // split n_items among graphs: round 0 (and policy 1) equal, else by weight
+    std::vector<unsigned int> cnt(k, 0);
+    double wsum = 0.0;
+    for (int g = 0; g < k; ++g) wsum += (r == 0 || o.policy == 1) ? 1.0 : weight[g];
+    unsigned int given = 0;
+    for (int g = 0; g < k; ++g) {
+      const double w = (r == 0 || o.policy == 1) ? 1.0 : weight[g];
+      cnt[g] = std::max(1u, unsigned(std::floor(double(n_items - k) * w / wsum)) + 1u);
+      given += cnt[g];
+    }
+    // hand out any remainder round-robin by weight order, trim any excess
+    int gi = 0;
+    while (given < n_items) { ++cnt[gi % k]; ++given; ++gi; }
+    while (given > n_items) { int gm = int(std::max_element(cnt.begin(), cnt.end()) - cnt.begin()); --cnt[gm]; --given; }
+    unsigned int it = 0;
+    for (int g = 0; g < k; ++g)
+      for (unsigned int j = 0; j < cnt[g]; ++j) {
+        hi[it].diag = uint32_t(g); hi[it].begin = next[g]; hi[it].count = uint32_t(chunk);
+        next[g] += chunk;
+        ++it;
+      }
+    if (gexec) { CUDA_TRY(cudaGraphLaunch(gexec, st)); }
+    else { int rc = enqueue_round(st); if (rc) return rc; }
+    launches += 2;
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (unsigned int i = 0; i < n_items; ++i) {
+      qed_result &q = R[hi[i].diag];
+      dd_acc(q.sum_w[0], q.sum_w[1], o_part[4 * i], o_part[4 * i + 1]);
+      dd_acc(q.sum_w2[0], q.sum_w2[1], o_part[4 * i + 2], o_part[4 * i + 3]);
+      dd_acc(q.sum_w[0], q.sum_w[1], o_pdd[4 * i], o_pdd[4 * i + 1]);
+      dd_acc(q.sum_w2[0], q.sum_w2[1], o_pdd[4 * i + 2], o_pdd[4 * i + 3]);
+      q.n += hi[i].count;
+      q.n_flagged += o_cnt[2 * i];
+      q.n_unstable += o_cdd[2 * i + 1];
+    }
+    // Neyman weights: sigma_g / sqrt(cost_g), cost = FP64 ops per sample with
+    // flagged samples counted at the double-double factor
+    for (int g = 0; g < k; ++g) {
+      finish(&R[g]);
+      const double var1 = R[g].variance * double(R[g].n);          // per-sample variance
+      double fl = 0.0;
+      qed_diagram_flops(d[g], &fl);
+      const double frac = R[g].n ? double(R[g].n_flagged) / double(R[g].n) : 0.0;
+      const double cost = fl * (1.0 + 12.0 * frac);
+      weight[g] = std::sqrt(std::max(var1, 0.0) / std::max(cost, 1.0));
+      if (!(weight[g] > 0.0) || !std::isfinite(weight[g])) weight[g] = 1e-300;
+    }
+  }
+  CUDA_TRY(cudaEventRecord(c->ev1, st));
+  CUDA_TRY(cudaEventSynchronize(c->ev1));
+  float ms = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (own_stream) cudaStreamDestroy(st);
+  for (int g = 0; g < k; ++g) {
+    finish(&R[g]);
+    R[g].seconds = ms * 1e-3;
+    R[g].kernel_seconds = 0.0;
+    R[g].launches = launches;
+    out[g] = R[g];
+  }
   return QED_OK;
 }
