@@ -72,7 +72,10 @@ def f2_from_parts(G0_11, Gi_12, Gi_21, Hij_11):
             for l in range(3):
                 if EPS[i, j, l] != 0.0:
                     mag = mag + EPS[i, j, l] * np.trace(SIG[l] @ X[..., i, j, :, :], axis1=-2, axis2=-1)
-    mag = mag * (1j / 12.0)
+    # i/12 applied as (times i) then (divide by 12): exact in the extended
+    # precision modes, where a rounded double 1/12 would be amplified by the
+    # cancellation between (F1 + F2) and F1
+    mag = mag * 1j / 12
     return mag - F1
 
 

@@ -272,10 +272,15 @@ class TermEvaluator:
 
     # ---- evaluate ---------------------------------------------------------
     def __call__(self, z, dtype=np.float64):
-        """dtype np.float64, or np.longdouble for the extended-precision
-        reference used to check re-evaluated (flagged) points."""
+        """dtype np.float64; np.longdouble; or object with mpmath numbers in z
+        (arbitrary precision, the reference for re-evaluated points)."""
         self.dtype = dtype
-        self.ctype = complex if dtype == np.float64 else np.clongdouble
+        if dtype == np.float64:
+            self.ctype = complex
+        elif dtype == np.longdouble:
+            self.ctype = np.clongdouble
+        else:                      # object: mpmath numbers, exact to mp.dps
+            self.ctype = object
         z = np.atleast_2d(np.asarray(z, dtype=dtype))
         P = polynomials(z, self.eta, self.alpha, self.beta, self.kappa, self.mass2, dtype=dtype)
         self.P = P

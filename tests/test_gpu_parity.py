@@ -69,25 +69,32 @@ def test_points_density_integrand_match_oracle(ctx, n, gi, begin, count):
     assert ok.mean() > 0.15
     rel = np.abs(f[ok] - fo[ok]) / np.abs(fo[ok])
     assert rel.max() < 1e-9, rel.max()
-    # strict check against the extended-precision (long double) oracle on a
-    # subsample: accepted FP64 values and double-double values of flagged
-    # points, both to 1e-12 relative
+    # strict check, 1e-12 relative, on a subsample: accepted FP64 values and
+    # double-double values of flagged points against the long-double oracle;
+    # where the two disagree (the oracle's own V = sum z - sum z A^2 cancels
+    # at IR corners, even in long double) the arbiter is the oracle in
+    # arbitrary precision (mpmath, 34 digits) on the four worst points
     sub = np.arange(0, count, 5)
-    fld = Integrand(og)(z[sub], dtype=np.longdouble)
-    # the oracle's own rounding: its long-double value is 2^11 times finer
-    # than its FP64 value, so the FP64-long-double gap / 2^11 estimates the
-    # long-double error (x8 margin); it matters only at the IR corners where
-    # the oracle's V = sum z - sum z A^2 cancels
-    ref_err = 8.0 * 2.0 ** -11 * np.abs(fo[sub] - fld.astype(np.float64))
-    fl_ld = fld.astype(np.float64)
-    tol = 1e-12 * np.abs(fl_ld) + ref_err
+    fld = Integrand(og)(z[sub], dtype=np.longdouble).astype(np.float64)
     zt = torch.tensor(z[sub], dtype=torch.float64, device="cuda")
     fdd = d.eval_points(zt, prec=1).cpu().numpy()
-    oks = ok[sub]
-    bad64 = np.abs(f[sub] - fl_ld) > tol
-    baddd = np.abs(fdd - fl_ld) > tol
-    assert not np.any(bad64 & oks), (np.abs(f[sub] - fl_ld) / np.abs(fl_ld))[bad64 & oks]
-    assert baddd.mean() < 0.01, (np.abs(fdd - fl_ld) / np.abs(fl_ld))[baddd]
+    gpu = np.where(ok[sub], f[sub], fdd)
+    rel = np.abs(gpu - fld) / np.abs(fld)
+    _arbitrate(og, z[sub], gpu, rel)
+
+
+def _arbitrate(og, zs, gpu, rel, n_check=4, tol=1e-12):
+    import mpmath
+    idx = np.argsort(-rel)[:n_check]
+    idx = [i for i in idx if rel[i] > tol]
+    if not idx:
+        return
+    with mpmath.workdps(34):
+        zo = np.array([[mpmath.mpf(float(v)) for v in zs[i]] for i in idx], dtype=object)
+        ref = Integrand(og)(zo, dtype=object)
+        for j, i in enumerate(idx):
+            r = abs(mpmath.mpf(float(gpu[i])) - ref[j]) / abs(ref[j])
+            assert r < tol, (i, float(r), gpu[i], float(ref[j]))
 
 
 @pytest.mark.parametrize("n,gi", GRAPHS)
@@ -104,10 +111,9 @@ def test_double_double_agrees_with_fp64_and_oracle(ctx, n, gi):
     sub = np.arange(0, 512, 8)
     og = o_enum(n)[gi]
     zz = z.cpu().numpy()[sub]
-    fld = Integrand(og)(zz, dtype=np.longdouble)
-    f64o = Integrand(og)(zz)
-    tol = 1e-12 * np.abs(fld.astype(np.float64)) + 8.0 * 2.0 ** -11 * np.abs(f64o - fld.astype(np.float64))
-    assert np.all(np.abs(fdd[sub] - fld.astype(np.float64)) <= tol)
+    fld = Integrand(og)(zz, dtype=np.longdouble).astype(np.float64)
+    rel = np.abs(fdd[sub] - fld) / np.abs(fld)
+    _arbitrate(og, zz, fdd[sub], rel)
 
 
 def test_one_loop_estimate_is_one_half(ctx):
