@@ -141,6 +141,20 @@ int qed_dump_points(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed,
  * (prec = 0) or double-double (prec = 1, result rounded to double). */
 int qed_eval_points(qed_diag *d, const double *z_dev, uint64_t n, int prec, double *f_dev);
 
+/* ---- tunable density and the adjoint of the second moment --------------- */
+/* Set the density's parameters theta (Sec. 2 builds the density from Deg;
+ * the paper's version is nonadaptive, these parameters only reshape it):
+ * Deg_theta(S) = max(d_min, Deg(S) + sum_{l in S} alpha[l]) and the first
+ * walk step weighted by exp(beta[j]).  alpha, beta: N doubles each (NULL =
+ * zeros).  The estimator stays unbiased for any finite theta. */
+int qed_diagram_set_pdf_params(qed_diag *d, const double *alpha, const double *beta);
+/* Adjoint of M2 = E_p[(f/p)^2], the second moment that sets the variance,
+ * over samples [begin, begin + n) recomputed from their Philox counters:
+ * *m2 = estimate of M2, grad[0..N-1] = dM2/dalpha, grad[N..2N-1] =
+ * dM2/dbeta (score-function form -E_p[w^2 d log p / d theta]; d log Z /
+ * d theta from a reverse pass over the F recursion on the host). */
+int qed_pdf_grad(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed, double *m2, double *grad);
+
 /* ---- batched integration of a graph set --------------------------------- */
 /* Options of qed_integrate_batch.  Zero-initialised fields take defaults. */
 typedef struct {

@@ -15,7 +15,7 @@
 #include "qed_kernels.cuh"
 
 struct BatchDiag {
-  const double *F, *G, *inv;
+  const double *F, *G, *inv, *off;
   double logZ;
   uint32_t stream;
   int fid;
@@ -46,7 +46,7 @@ struct BatchParams {
 
 __device__ __forceinline__ KParams batch_kparams(const BatchParams &B, const BatchDiag &D) {
   KParams P;
-  P.F = D.F; P.G = D.G; P.invdeg = D.inv;
+  P.F = D.F; P.G = D.G; P.invdeg = D.inv; P.off = D.off;
   P.logZ = D.logZ;
   P.begin = 0; P.n = 0;
   P.key0 = B.key0; P.key1 = B.key1; P.stream = D.stream;

@@ -38,7 +38,8 @@ struct KParams {
   const double *F;        // F(S), 2^N
   const double *G;        // F(S) / Deg(S), 2^N
   const double *invdeg;   // 1 / Deg(S), 2^N
-  double logZ;            // log F(E)
+  double logZ;            // log Z (normaliser of Eq. (1) with the sector weights)
+  const double *off;      // [N] beta_j - log Z: log p offset of a point whose largest line is j
   uint64_t begin, n;
   uint32_t key0, key1, stream;
   double thresh;          // relative rounding-error threshold
@@ -63,12 +64,15 @@ __device__ __forceinline__ double rel_err_estimate(double f, double absum, doubl
 }
 
 // Draw the point of sample `s`: z[line] (largest component 1) and log p.
-// Tables live in shared memory (sF, sG, sInv); xs is this thread's scratch
-// row in shared memory.
-template <int N>
+// Tables live in shared memory: sF (F), sG (F / Deg, with the sector weight
+// folded into the sets of N-1 lines), sInv (1 / Deg), and sInv + 2^N holds
+// the N first-line offsets beta_j - log Z.  With GRAD the sector order and
+// log t_l (l = 1..N-1) are returned for the adjoint kernel.
+template <int N, bool GRAD = false>
 __device__ __forceinline__ double draw_point(uint64_t s, const KParams &P, const double *__restrict__ sF,
                                              const double *__restrict__ sG, const double *__restrict__ sInv,
-                                             double *__restrict__ z) {
+                                             double *__restrict__ z, int *order_out = nullptr,
+                                             double *logt_out = nullptr) {
   constexpr int ND = 2 * (N - 1);
   double u[ND];
 #pragma unroll
@@ -99,7 +103,7 @@ __device__ __forceinline__ double draw_point(uint64_t s, const KParams &P, const
   }
   order[N - 1] = __ffs(S) - 1;
   // radial variables: t_l = u^(1/Deg(S_l)), z_{j_l} = z_{j_(l-1)} t_l
-  double lp = -P.logZ, logx = 0.0;
+  double lp = sInv[(1 << N) + order[0]], logx = 0.0;
   S = full;
   double xs[N];
   xs[0] = 1.0;
@@ -107,9 +111,15 @@ __device__ __forceinline__ double draw_point(uint64_t s, const KParams &P, const
   for (int l = 1; l < N; ++l) {
     S &= ~(1u << order[l - 1]);
     const double lu = log(u[N - 1 + (l - 1)]);
-    logx += lu * sInv[S];
+    const double lt = lu * sInv[S];
+    logx += lt;
     xs[l] = exp(logx);
     lp += lu - logx;
+    if (GRAD) logt_out[l] = lt;
+  }
+  if (GRAD) {
+#pragma unroll
+    for (int l = 0; l < N; ++l) order_out[l] = order[l];
   }
   // scatter sector order -> line index with constant register indices
 #pragma unroll
@@ -129,6 +139,7 @@ __device__ __forceinline__ void load_tables(const KParams &P, double *sF, double
     sG[i] = P.G[i];
     sInv[i] = P.invdeg[i];
   }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sInv[(1 << N) + i] = P.off[i];
   __syncthreads();
 }
 
@@ -291,14 +302,77 @@ __global__ void __launch_bounds__(256) k_eval(const double *__restrict__ zin, ui
 }
 
 
+// Adjoint of the second moment M2 = E_p[w^2] with respect to the density's
+// parameters (per-line Deg shifts alpha_m, first-level sector weights
+// beta_m): accumulates, over samples recomputed from their Philox counters,
+//   w^2,  w^2 * sum_{l: m in S_l, Deg(S_l) not clamped} log t_l,  w^2 [j_1 = m].
+// The host adds the d log Z / d theta terms (reverse pass over the F table).
+// out: [gridDim.x][2N + 1] (w^2, the N alpha sums, the N beta sums).
+template <int FID, int N>
+__global__ void __launch_bounds__(256) k_pdf_grad(KParams P, const uint8_t *__restrict__ act, double *out) {
+  extern __shared__ double smem[];
+  double *sF = smem, *sG = smem + (1 << N), *sInv = smem + 2 * (1 << N);
+  load_tables<N>(P, sF, sG, sInv);
+  double m2 = 0.0, ga[N], gb[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) { ga[m] = 0.0; gb[m] = 0.0; }
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P.n; i += stride) {
+    double z[N], lt[N];
+    int order[N];
+    const double lp = draw_point<N, true>(P.begin + i, P, sF, sG, sInv, z, order, lt);
+    double absum;
+    const double f = qed_gen_f<FID>::template eval<double>(z, absum);
+    double w = f * exp(-lp);
+    if (!isfinite(w)) w = 0.0;
+    const double w2 = w * w;
+    m2 += w2;
+    // cumulative sum over sector positions: line at position r gets
+    // sum_{l=1..r} act(S_l) log t_l
+    double cum = 0.0;
+    uint32_t S = (1u << N) - 1u;
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      if (r > 0) {
+        S &= ~(1u << order[r - 1]);
+        if (act[S]) cum += lt[r];
+      }
+#pragma unroll
+      for (int m = 0; m < N; ++m) if (order[r] == m) ga[m] += w2 * cum;
+    }
+#pragma unroll
+    for (int m = 0; m < N; ++m) if (order[0] == m) gb[m] += w2;
+  }
+  // block reduction (warp shuffles, then shared memory), fixed order
+  __shared__ double red[32][2 * N + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double v[2 * N + 1];
+  v[0] = m2;
+#pragma unroll
+  for (int m = 0; m < N; ++m) { v[1 + m] = ga[m]; v[1 + N + m] = gb[m]; }
+#pragma unroll
+  for (int k = 0; k < 2 * N + 1; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0) red[warp][k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * N + 1) {
+    double acc = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) acc += red[w][threadIdx.x];
+    out[size_t(blockIdx.x) * (2 * N + 1) + threadIdx.x] = acc;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // per-graph kernel set
 // ---------------------------------------------------------------------------
 struct KernelSet {
-  const void *integrate, *redo, *dump, *eval;
+  const void *integrate, *redo, *dump, *eval, *grad;
   int lines;
 };
 #define QED_DEFINE_KSET(id, lines)                                                              \
   extern const KernelSet qed_kset_##id;                                                        \
   const KernelSet qed_kset_##id = {(const void *)k_integrate<id, lines>, (const void *)k_redo_dd<id, lines>, \
-                                   (const void *)k_dump<id, lines>, (const void *)k_eval<id, lines>, lines};
+                                   (const void *)k_dump<id, lines>, (const void *)k_eval<id, lines>,            \
+                                   (const void *)k_pdf_grad<id, lines>, lines};

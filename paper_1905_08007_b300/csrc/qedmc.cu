@@ -81,8 +81,60 @@ struct qed_diag {
   int fid = -1;
   int N = 0;
   double logZ = 0.0;
-  double *d_tab = nullptr;   // F, G, invdeg consecutively
+  double d_min = 0.05;
+  std::vector<double> deg0;          // Deg(S) before the tunable shifts
+  std::vector<double> alpha, beta;   // per-line Deg shifts, first-level sector weights
+  std::vector<double> deg, F;        // current Deg_theta and F tables
+  std::vector<uint8_t> act;          // Deg_theta(S) not clamped at d_min
+  double *d_tab = nullptr;           // F, G, 1/Deg (3 x 2^N), then N first-line offsets
+  uint8_t *d_act = nullptr;          // 2^N activity flags (adjoint kernel)
 };
+
+// Deg_theta(S) = max(d_min, Deg0(S) + sum_{l in S} alpha_l); the first walk
+// step picks line j with weight e^{beta_j} F(E\j) / Deg(E\j), so
+// Z = sum_j e^{beta_j} F(E\j) / Deg(E\j) and log p gains beta_{j_1} - log Z.
+static int rebuild_tables(qed_diag *d) {
+  const int N = d->N;
+  const size_t M = size_t(1) << N;
+  d->deg.assign(M, 0.0);
+  d->act.assign(M, 0);
+  for (size_t m = 1; m + 1 < M; ++m) {
+    double v = d->deg0[m];
+    for (int l = 0; l < N; ++l) if (m >> l & 1) v += d->alpha[l];
+    if (v > d->d_min) { d->deg[m] = v; d->act[m] = 1; }
+    else d->deg[m] = d->d_min;
+    if (!std::isfinite(d->deg[m])) return set_err(QED_EINVAL, "Deg not finite");
+  }
+  d->F.assign(M, 0.0);
+  std::vector<double> G(M, 0.0), inv(M, 0.0), off(N, 0.0);
+  for (size_t m = 1; m + 1 < M; ++m) {
+    if (__builtin_popcountll(m) == 1) { d->F[m] = 1.0; continue; }
+    double acc = 0.0;
+    for (int j = 0; j < N; ++j) if (m >> j & 1) { size_t r = m & ~(size_t(1) << j); acc += d->F[r] / d->deg[r]; }
+    d->F[m] = acc;
+  }
+  for (size_t m = 1; m + 1 < M; ++m) { G[m] = d->F[m] / d->deg[m]; inv[m] = 1.0 / d->deg[m]; }
+  double Z = 0.0;
+  for (int j = 0; j < N; ++j) {
+    const size_t r = (M - 1) & ~(size_t(1) << j);
+    G[r] *= std::exp(d->beta[j]);
+    Z += G[r];
+  }
+  std::vector<double> Ft = d->F;
+  Ft[M - 1] = Z;
+  d->F[M - 1] = Z;
+  d->logZ = std::log(Z);
+  for (int j = 0; j < N; ++j) off[j] = d->beta[j] - d->logZ;
+  CUDA_TRY(cudaSetDevice(d->ctx->device));
+  CUDA_TRY(cudaMemcpy(d->d_tab, Ft.data(), M * sizeof(double), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(d->d_tab + M, G.data(), M * sizeof(double), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(d->d_tab + 2 * M, inv.data(), M * sizeof(double), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(d->d_tab + 3 * M, off.data(), N * sizeof(double), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(d->d_act, d->act.data(), M, cudaMemcpyHostToDevice));
+  return QED_OK;
+}
+
+static size_t table_smem(int N) { return (3 * (size_t(1) << N) + size_t(N)) * sizeof(double); }
 
 static int ensure_scratch(qed_ctx *c, int blocks) {
   if (blocks <= c->partial_cap) return QED_OK;
@@ -212,6 +264,7 @@ extern "C" int qed_gauge_class(const qed_graph *in, int kmn[3]) {
   return QED_OK;
 }
 
+extern "C" int qed_diagram_free(qed_diag *d);
 extern "C" int qed_diagram_load(qed_ctx *ctx, const qed_graph *gin, const qed_pdf *pdf, qed_diag **out) {
   if (!ctx || !out) return set_err(QED_EINVAL, "ctx/out is NULL");
   qed::Graph g;
@@ -223,32 +276,28 @@ extern "C" int qed_diagram_load(qed_ctx *ctx, const qed_graph *gin, const qed_pd
   if (fid < 0) return set_err(QED_ENOTFOUND, "no generated integrand for " + nm);
   const int N = g.n_lines();
   const size_t M = size_t(1) << N;
-  std::vector<double> deg;
+  qed_diag *d = new qed_diag();
+  d->ctx = ctx; d->g = g; d->stream_id = gin->stream_id; d->fid = fid; d->N = N;
   if (pdf && pdf->deg) {
-    deg.assign(pdf->deg, pdf->deg + M);
+    d->deg0.assign(pdf->deg, pdf->deg + M);
     for (size_t m = 1; m + 1 < M; ++m)
-      if (!(deg[m] > 0.0) || !std::isfinite(deg[m])) return set_err(QED_EINVAL, "Deg must be positive and finite on every proper subset");
+      if (!(d->deg0[m] > 0.0) || !std::isfinite(d->deg0[m])) { delete d; return set_err(QED_EINVAL, "Deg must be positive and finite on every proper subset"); }
+    d->d_min = 1e-300;   // a caller's table is used as given (no floor)
   } else {
     double c_div = (pdf && pdf->c_div > 0) ? pdf->c_div : 0.5;
-    double d_min = (pdf && pdf->d_min > 0) ? pdf->d_min : 0.05;
-    deg = qed::deg_table(g, c_div, d_min);
+    d->d_min = (pdf && pdf->d_min > 0) ? pdf->d_min : 0.05;
+    d->deg0 = qed::deg_table(g, c_div, d->d_min);
   }
-  // F(S) = sum_{j in S, ascending} F(S \ j) / Deg(S \ j), F({x}) = 1
-  std::vector<double> F(M, 0.0), G(M, 0.0), inv(M, 0.0);
-  for (size_t m = 1; m < M; ++m) {
-    if (__builtin_popcountll(m) == 1) { F[m] = 1.0; continue; }
-    double acc = 0.0;
-    for (int j = 0; j < N; ++j) if (m >> j & 1) { size_t r = m & ~(size_t(1) << j); acc += F[r] / deg[r]; }
-    F[m] = acc;
-  }
-  for (size_t m = 1; m + 1 < M; ++m) { G[m] = F[m] / deg[m]; inv[m] = 1.0 / deg[m]; }
-  qed_diag *d = new qed_diag();
-  d->ctx = ctx; d->g = g; d->stream_id = gin->stream_id; d->fid = fid; d->N = N; d->logZ = std::log(F[M - 1]);
+  d->alpha.assign(N, 0.0);
+  d->beta.assign(N, 0.0);
   CUDA_TRY(cudaSetDevice(ctx->device));
-  if (cudaMalloc(&d->d_tab, 3 * M * sizeof(double)) != cudaSuccess) { delete d; return set_err(QED_ENOMEM, "table allocation"); }
-  CUDA_TRY(cudaMemcpy(d->d_tab, F.data(), M * sizeof(double), cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(d->d_tab + M, G.data(), M * sizeof(double), cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(d->d_tab + 2 * M, inv.data(), M * sizeof(double), cudaMemcpyHostToDevice));
+  if (cudaMalloc(&d->d_tab, (3 * M + N) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&d->d_act, M) != cudaSuccess) {
+    qed_diagram_free(d);
+    return set_err(QED_ENOMEM, "table allocation");
+  }
+  int rc = rebuild_tables(d);
+  if (rc) { qed_diagram_free(d); return rc; }
   *out = d;
   return QED_OK;
 }
@@ -257,6 +306,7 @@ extern "C" int qed_diagram_free(qed_diag *d) {
   if (!d) return QED_OK;
   cudaSetDevice(d->ctx->device);
   if (d->d_tab) cudaFree(d->d_tab);
+  if (d->d_act) cudaFree(d->d_act);
   delete d;
   return QED_OK;
 }
@@ -276,7 +326,7 @@ static KParams base_params(const qed_diag *d, uint64_t begin, uint64_t n, uint64
   KParams P;
   std::memset(&P, 0, sizeof P);
   const size_t M = size_t(1) << d->N;
-  P.F = d->d_tab; P.G = d->d_tab + M; P.invdeg = d->d_tab + 2 * M;
+  P.F = d->d_tab; P.G = d->d_tab + M; P.invdeg = d->d_tab + 2 * M; P.off = d->d_tab + 3 * M;
   P.logZ = d->logZ;
   P.begin = begin; P.n = n;
   P.key0 = uint32_t(seed); P.key1 = uint32_t(seed >> 32);
@@ -331,7 +381,7 @@ extern "C" int qed_integrate_range(qed_diag *d, uint64_t begin, uint64_t n, uint
   const int blocks = c->blocks > 0 ? c->blocks : 4 * c->sms;
   int rc = ensure_scratch(c, blocks);
   if (rc) return rc;
-  const size_t smem = 3 * (size_t(1) << d->N) * sizeof(double);
+  const size_t smem = table_smem(d->N);
   qed_result r;
   std::memset(&r, 0, sizeof r);
   r.n = n;
@@ -387,7 +437,7 @@ extern "C" int qed_dump_points(qed_diag *d, uint64_t begin, uint64_t n, uint64_t
   const int threads = c->threads;
   const int blocks = int(std::max<uint64_t>(1, std::min<uint64_t>((n + threads - 1) / threads, uint64_t(c->sms) * 8)));
   void *args[] = {&P};
-  int rc = launch(g_kernels[d->fid]->dump, blocks, threads, 3 * (size_t(1) << d->N) * sizeof(double), c->stream, args);
+  int rc = launch(g_kernels[d->fid]->dump, blocks, threads, table_smem(d->N), c->stream, args);
   if (rc) return rc;
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   return QED_OK;
@@ -521,7 +571,7 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
   const uint32_t list_cap = uint32_t(std::max<uint64_t>(1, chunk / list_div));
   int Nmax = 0;
   for (int g = 0; g < k; ++g) Nmax = std::max(Nmax, d[g]->N);
-  const size_t smem = 3 * (size_t(1) << Nmax) * sizeof(double);
+  const size_t smem = table_smem(Nmax);
   // device and pinned buffers
   DevBuf dd_diags, dd_items, dd_next, dd_part, dd_cnt, dd_lists, dd_pdd, dd_cdd;
   HostBuf h_items, h_out;
@@ -539,7 +589,7 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
   std::vector<BatchDiag> hd(k);
   for (int g = 0; g < k; ++g) {
     const size_t M = size_t(1) << d[g]->N;
-    hd[g].F = d[g]->d_tab; hd[g].G = d[g]->d_tab + M; hd[g].inv = d[g]->d_tab + 2 * M;
+    hd[g].F = d[g]->d_tab; hd[g].G = d[g]->d_tab + M; hd[g].inv = d[g]->d_tab + 2 * M; hd[g].off = d[g]->d_tab + 3 * M;
     hd[g].logZ = d[g]->logZ; hd[g].stream = d[g]->stream_id; hd[g].fid = d[g]->fid; hd[g].N = d[g]->N; hd[g].pad = 0;
   }
   CUDA_TRY(cudaMemcpy(dd_diags.p, hd.data(), sizeof(BatchDiag) * k, cudaMemcpyHostToDevice));
@@ -655,5 +705,85 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
     R[g].launches = launches;
     out[g] = R[g];
   }
+  return QED_OK;
+}
+
+// ---------------------------------------------------------------------------
+// tunable density parameters and the adjoint of the second moment
+// ---------------------------------------------------------------------------
+extern "C" int qed_diagram_set_pdf_params(qed_diag *d, const double *alpha, const double *beta) {
+  if (!d) return set_err(QED_EINVAL, "diag is NULL");
+  for (int l = 0; l < d->N; ++l) {
+    d->alpha[l] = alpha ? alpha[l] : 0.0;
+    d->beta[l] = beta ? beta[l] : 0.0;
+    if (!std::isfinite(d->alpha[l]) || !std::isfinite(d->beta[l])) return set_err(QED_EINVAL, "parameters must be finite");
+  }
+  return rebuild_tables(d);
+}
+
+// d log Z / d theta by a reverse pass over the F recursion.
+static void dlogz(const qed_diag *d, std::vector<double> &ga, std::vector<double> &gb) {
+  const int N = d->N;
+  const size_t M = size_t(1) << N;
+  const std::vector<double> &D = d->deg, &F = d->F;
+  std::vector<double> Fb(M, 0.0), Db(M, 0.0);
+  const double Z = F[M - 1];
+  ga.assign(N, 0.0);
+  gb.assign(N, 0.0);
+  for (int j = 0; j < N; ++j) {
+    const size_t r = (M - 1) & ~(size_t(1) << j);
+    const double e = std::exp(d->beta[j]) / Z;
+    Fb[r] += e / D[r];
+    Db[r] -= e * F[r] / (D[r] * D[r]);
+    gb[j] = e * F[r] / D[r];
+  }
+  // sets in decreasing size: F(S) = sum_j F(S\j) / D(S\j)
+  std::vector<size_t> order;
+  for (size_t m = 1; m + 1 < M; ++m) order.push_back(m);
+  std::sort(order.begin(), order.end(), [](size_t a, size_t b) { return __builtin_popcountll(a) > __builtin_popcountll(b); });
+  for (size_t m : order) {
+    if (__builtin_popcountll(m) < 2 || Fb[m] == 0.0) continue;
+    for (int j = 0; j < N; ++j) if (m >> j & 1) {
+      const size_t r = m & ~(size_t(1) << j);
+      Fb[r] += Fb[m] / D[r];
+      Db[r] -= Fb[m] * F[r] / (D[r] * D[r]);
+    }
+  }
+  for (size_t m = 1; m + 1 < M; ++m)
+    if (d->act[m] && Db[m] != 0.0)
+      for (int l = 0; l < N; ++l) if (m >> l & 1) ga[l] += Db[m];
+}
+
+extern "C" int qed_pdf_grad(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed, double *m2, double *grad) {
+  if (!d || !m2 || !grad || n == 0) return set_err(QED_EINVAL, "bad argument");
+  qed_ctx *c = d->ctx;
+  CUDA_TRY(cudaSetDevice(c->device));
+  const int N = d->N;
+  const int blocks = 4 * c->sms, threads = 256;
+  double *dout = nullptr;
+  CUDA_TRY(cudaMalloc(&dout, sizeof(double) * blocks * (2 * N + 1)));
+  KParams P = base_params(d, begin, n, seed);
+  const uint8_t *act = d->d_act;
+  void *args[] = {&P, (void *)&act, &dout};
+  int rc = launch(g_kernels[d->fid]->grad, blocks, threads, table_smem(N), c->stream, args);
+  std::vector<double> h(size_t(blocks) * (2 * N + 1));
+  if (!rc) {
+    cudaError_t e = cudaMemcpyAsync(h.data(), dout, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) rc = set_err(QED_ECUDA, cudaGetErrorString(e));
+  }
+  cudaFree(dout);
+  if (rc) return rc;
+  std::vector<double> acc(2 * N + 1, 0.0);
+  for (int b = 0; b < blocks; ++b)
+    for (int k = 0; k < 2 * N + 1; ++k) acc[k] += h[size_t(b) * (2 * N + 1) + k];
+  const double M2 = acc[0] / double(n);
+  std::vector<double> ga, gb;
+  dlogz(d, ga, gb);
+  for (int m = 0; m < N; ++m) {
+    grad[m] = -(acc[1 + m] / double(n) - M2 * ga[m]);
+    grad[N + m] = -(acc[1 + N + m] / double(n) - M2 * gb[m]);
+  }
+  *m2 = M2;
   return QED_OK;
 }
