@@ -1,0 +1,70 @@
+"""GPU tests of the density adjoint: the library's M2 and dM2/dtheta equal the
+oracle's score-function estimate on the same Philox points; the tuned density
+samples from the oracle's tuned sampler point for point; gradient descent
+through the torch.autograd.Function lowers the second moment while the mean
+stays within its error."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1905_08007_b300 as q                         # noqa: E402
+from paper_1905_08007_b300.tune import pdf_grad, tune, _set_params   # noqa: E402
+from oracle.adjoint import m2_grad, sample_theta           # noqa: E402
+from oracle.graphs import deg_table, enumerate_graphs as o_enum  # noqa: E402
+from oracle.integrand import Integrand                     # noqa: E402
+from oracle.philox import uniforms                         # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return q.Context(0)
+
+
+THETA = {3: ([0.2, -0.1, 0.15], [0.1, 0.0, -0.2]),
+         6: ([0.1, -0.05, 0.2, 0.0, -0.1, 0.05], [0.2, -0.1, 0.0, 0.1, -0.2, 0.3])}
+
+
+@pytest.mark.parametrize("n,gi", [(1, 0), (2, 0), (2, 4)])
+def test_tuned_points_match_oracle(ctx, n, gi):
+    g = q.enumerate_graphs(n)[gi]
+    og = o_enum(n)[gi]
+    d = ctx.load(g)
+    a, b = THETA[og.n_lines]
+    _set_params(d, a, b)
+    z, f, lp, fl = d.dump_points(0, 777, seed=2)
+    N = og.n_lines
+    u = uniforms(np.arange(777), g.stream_id, 2, 2 * (N - 1))
+    x, lpo, *_ = sample_theta(u, deg_table(og), a, b, N)
+    np.testing.assert_allclose(z.cpu().numpy(), x, rtol=1e-12)
+    np.testing.assert_allclose(lp.cpu().numpy(), lpo, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("n,gi,tol", [(1, 0, 1e-10), (2, 0, 1e-6), (2, 4, 1e-6)])
+def test_gradient_matches_oracle_on_same_points(ctx, n, gi, tol):
+    g = q.enumerate_graphs(n)[gi]
+    og = o_enum(n)[gi]
+    d = ctx.load(g)
+    a, b = THETA[og.n_lines]
+    cnt = 3000 + 17
+    m2, ga, gb = pdf_grad(d, a, b, cnt, seed=7, begin=123)
+    m2o, gao, gbo = m2_grad(Integrand(og), og, g.stream_id, 7, 123, cnt, a, b)
+    assert m2 == pytest.approx(m2o, rel=tol)
+    scale = max(np.max(np.abs(gao)), np.max(np.abs(gbo)))
+    np.testing.assert_allclose(ga, gao, rtol=tol, atol=tol * scale)
+    np.testing.assert_allclose(gb, gbo, rtol=tol, atol=tol * scale)
+
+
+def test_tuning_lowers_second_moment_unbiased(ctx):
+    g = q.enumerate_graphs(2)[1]
+    d = ctx.load(g)
+    before = d.integrate(1 << 24, seed=21)
+    a, b, hist = tune(d, steps=12, n=1 << 21, lr=0.08)
+    after = d.integrate(1 << 24, seed=21)
+    assert after.variance < before.variance
+    assert abs(after.value - before.value) < 4 * math.sqrt(after.variance + before.variance)
