@@ -119,6 +119,39 @@ def cpu_baseline(n_per_graph=300, seed=0):
                       f"(Philox counters 1e12.., seed {seed}), {dt:.1f} s"}
 
 
+def compare_batched(q, ctx, graphs, diags, S, seed, t_step_plain, sigma_plain_run):
+    """Time to the target sigma on the whole set: the plain path (equal
+    samples per graph, untuned Eq. (1) densities, one launch per graph) vs
+    the batched path (gradient-tuned densities, variance-driven allocation in
+    one persistent launch per round).  Tuning time is reported separately."""
+    from paper_1905_08007_b300.tune import tune
+    total = S * len(diags)
+    # plain: one step of the timed loop (same samples), sigma of its total
+    plain = [d.integrate(S, seed=seed + 1, begin=0) for d in diags]
+    t_plain = sum(r.seconds for r in plain)
+    sig_plain = math.sqrt(sum(r.variance for r in plain))
+    t0 = time.perf_counter()
+    for d in diags:
+        tune(d, steps=10, n=1 << 21, lr=0.08, seed=seed + 7)
+    t_tune = time.perf_counter() - t0
+    res = ctx.integrate_batch(diags, total, seed=seed + 2, policy="variance", rounds=4, chunk=1 << 18)
+    t_batch = res[0].seconds
+    sig_batch = math.sqrt(sum(r.variance for r in res))
+    val_batch = sum(r.value for r in res)
+    for d in diags:       # back to the untuned densities
+        from paper_1905_08007_b300.tune import _set_params
+        _set_params(d, [0.0] * d.n_lines, [0.0] * d.n_lines)
+    tts_plain = t_plain * (sig_plain / SIGMA_TARGET) ** 2
+    tts_batch = t_batch * (sig_batch / SIGMA_TARGET) ** 2
+    return {"target_sigma": SIGMA_TARGET, "samples": total,
+            "plain": {"seconds": t_plain, "sigma": sig_plain, "time_to_sigma": tts_plain,
+                      "samples_per_s": total / t_plain},
+            "batched_tuned": {"seconds": t_batch, "sigma": sig_batch, "time_to_sigma": tts_batch,
+                              "samples_per_s": sum(r.n for r in res) / t_batch, "total": val_batch,
+                              "samples_per_graph": [r.n for r in res], "tuning_seconds": t_tune},
+            "speedup_time_to_sigma": tts_plain / tts_batch}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -270,6 +303,8 @@ def run_native(args):
                 "d2h_bytes_per_step": d2h},
         "clocks": clk,
     }
+    if ws == 1 and args.compare:
+        line["batched_tuned"] = compare_batched(q, ctx, graphs, diags, S, args.seed, tmax / args.steps, sigma)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
@@ -288,6 +323,8 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--ref-samples", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", dest="compare", action="store_false",
+                    help="skip the plain vs batched-tuned time-to-sigma comparison")
     a = ap.parse_args(argv)
     if a.warmup < 3:
         a.warmup = 3
