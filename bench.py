@@ -130,25 +130,27 @@ def compare_batched(q, ctx, graphs, diags, S, seed, t_step_plain, sigma_plain_ru
     plain = [d.integrate(S, seed=seed + 1, begin=0) for d in diags]
     t_plain = sum(r.seconds for r in plain)
     sig_plain = math.sqrt(sum(r.variance for r in plain))
+    # tuned path on its own copies of the graphs: Deg calibrated on the
+    # integrand's measured limits, then gradient-tuned (alpha, beta)
+    tuned = [ctx.load(g) for g in graphs]
     t0 = time.perf_counter()
-    for d in diags:
+    for d in tuned:
+        d.calibrate_deg(n_base=8, seed=seed + 5)
         tune(d, steps=10, n=1 << 21, lr=0.08, seed=seed + 7)
     t_tune = time.perf_counter() - t0
-    res = ctx.integrate_batch(diags, total, seed=seed + 2, policy="variance", rounds=4, chunk=1 << 18)
+    res = ctx.integrate_batch(tuned, total, seed=seed + 2, policy="variance", rounds=4, chunk=1 << 18)
     t_batch = res[0].seconds
     sig_batch = math.sqrt(sum(r.variance for r in res))
     val_batch = sum(r.value for r in res)
-    for d in diags:       # back to the untuned densities
-        from paper_1905_08007_b300.tune import _set_params
-        _set_params(d, [0.0] * d.n_lines, [0.0] * d.n_lines)
     tts_plain = t_plain * (sig_plain / SIGMA_TARGET) ** 2
     tts_batch = t_batch * (sig_batch / SIGMA_TARGET) ** 2
     return {"target_sigma": SIGMA_TARGET, "samples": total,
             "plain": {"seconds": t_plain, "sigma": sig_plain, "time_to_sigma": tts_plain,
-                      "samples_per_s": total / t_plain},
+                      "samples_per_s": total / t_plain, "total": sum(r.value for r in plain)},
             "batched_tuned": {"seconds": t_batch, "sigma": sig_batch, "time_to_sigma": tts_batch,
                               "samples_per_s": sum(r.n for r in res) / t_batch, "total": val_batch,
-                              "samples_per_graph": [r.n for r in res], "tuning_seconds": t_tune},
+                              "samples_per_graph": [r.n for r in res], "tuning_seconds": t_tune,
+                              "pull": (val_batch - TWO_LOOP_TARGET) / sig_batch},
             "speedup_time_to_sigma": tts_plain / tts_batch}
 
 

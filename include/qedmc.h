@@ -155,6 +155,17 @@ int qed_diagram_set_pdf_params(qed_diag *d, const double *alpha, const double *b
  * d theta from a reverse pass over the F recursion on the host). */
 int qed_pdf_grad(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed, double *m2, double *grad);
 
+/* Calibrate Deg on the integrand itself (Sec. 2: Deg(s) "is not fully
+ * justified mathematically"; the paper lowers it for infrared limits).  For
+ * every proper subset s the growth exponent a_s of the integrand under
+ * z_s -> eps z_s is measured on the GPU in double-double at n_base random
+ * points (eps = 1e-4 and 1e-6) and Deg(s) is capped at |s| - a_s, where w =
+ * f/p stays bounded: Deg(s) = max(d_min, min(Deg(s), |s| - a_s)).
+ * Allocates two small device buffers for the duration of the call. */
+int qed_diagram_calibrate_deg(qed_diag *d, int n_base, uint64_t seed);
+/* The current Deg table (2^N doubles, bitmask-indexed). */
+int qed_diagram_get_deg(const qed_diag *d, double *deg_out);
+
 /* ---- batched integration of a graph set --------------------------------- */
 /* Options of qed_integrate_batch.  Zero-initialised fields take defaults. */
 typedef struct {

@@ -144,6 +144,8 @@ def load_library():
         "qed_integrate_batch": (C.c_int, [C.c_void_p, P(C.c_void_p), C.c_int, C.c_uint64, C.c_uint64,
                                           P(_BatchOpts), P(_Result)]),
         "qed_fp64_peak": (C.c_int, [C.c_int, C.c_double, P(C.c_double)]),
+        "qed_diagram_calibrate_deg": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64]),
+        "qed_diagram_get_deg": (C.c_int, [C.c_void_p, P(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -289,6 +291,16 @@ class Diagram:
         torch.cuda.synchronize(z.device)
         _check(load_library().qed_eval_points(self._h, z.data_ptr(), z.shape[0], prec, f.data_ptr()))
         return f
+
+    def calibrate_deg(self, n_base: int = 8, seed: int = 0):
+        """Cap Deg(s) by the measured growth of the integrand in each limit."""
+        _check(load_library().qed_diagram_calibrate_deg(self._h, n_base, seed))
+
+    def deg_table(self):
+        """The current Deg table as a list of 2^N floats."""
+        out = (C.c_double * (1 << self.n_lines))()
+        _check(load_library().qed_diagram_get_deg(self._h, out))
+        return list(out)
 
     def flops_per_sample(self) -> float:
         v = C.c_double()

@@ -452,6 +452,10 @@ struct Emitter {
   std::ostringstream os;
   int tmp = 0;
   std::string fresh(const char *p) { return std::string(p) + std::to_string(tmp++); }
+  // polynomials already emitted in this graph's function, by content key:
+  // forest terms with the same block structure share U, 1/U, B_ij, and with
+  // the same kinematics also (1 +- A), C, K and V
+  std::map<std::string, std::string> cache;
 };
 
 // Emit a sum of z's (as R expression); returns "" if empty
@@ -485,6 +489,33 @@ struct Poly {
     }
     r.clean();
     return r;
+  }
+  // nested (Horner-like) form over named variables (names[v] replaces z[v])
+  std::string horner_named(const std::vector<std::string> &names) const {
+    if (t.empty()) return "R(0.0)";
+    std::map<int, int> freq;
+    for (auto &kv : t) { std::set<int> u(kv.first.begin(), kv.first.end()); for (int v : u) ++freq[v]; }
+    if (freq.empty()) return "R(" + dstr(t.begin()->second) + ")";
+    int best = -1, bc = 0;
+    for (auto &kv : freq) if (kv.second > bc) { bc = kv.second; best = kv.first; }
+    Poly with, without;
+    for (auto &kv : t) {
+      auto it = std::find(kv.first.begin(), kv.first.end(), best);
+      if (it == kv.first.end()) { without.t[kv.first] = kv.second; continue; }
+      std::vector<int> m = kv.first;
+      m.erase(m.begin() + (it - kv.first.begin()));
+      with.t[m] = kv.second;
+    }
+    const std::string &zv = names[best];
+    std::string inner;
+    if (with.t.size() == 1 && with.t.begin()->first.empty()) {
+      double c = with.t.begin()->second;
+      inner = (c == 1.0) ? zv : "R(" + dstr(c) + ") * " + zv;
+    } else {
+      inner = zv + " * (" + with.horner_named(names) + ")";
+    }
+    if (without.zero()) return inner;
+    return inner + " + " + without.horner_named(names);
   }
   // nested (Horner-like) form: factor out the most frequent variable
   std::string horner() const {
@@ -568,9 +599,21 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
   std::vector<std::vector<Poly>> adjp(n, std::vector<Poly>(n));
   for (int a = 0; a < n; ++a)
     for (int b = 0; b < n; ++b) adjp[a][b] = cofactor_poly(lam, b, a);
-  std::string U = P + "_U";
-  os << "    const R " << U << " = " << Up.horner() << ";\n";
-  os << "    const R " << P << "_iU = R(1.0) / " << U << ";\n";
+  std::string eta_key;
+  for (int l = 0; l < L; ++l) { for (int a = 0; a < n; ++a) eta_key += char('0' + T.eta[l][a]); eta_key += '|'; }
+  auto vec_key = [](const std::vector<double> &v) { std::string k; for (double x : v) k += dstr(x) + ","; return k; };
+  std::string U, iU;
+  {
+    auto it = E.cache.find("U" + eta_key);
+    if (it != E.cache.end()) { U = it->second; iU = it->second + "_inv"; }
+    else {
+      U = P + "_U"; iU = U + "_inv";
+      os << "    const R " << U << " = " << Up.horner() << ";\n";
+      os << "    const R " << iU << " = R(1.0) / " << U << ";\n";
+      E.cache["U" + eta_key] = U;
+    }
+  }
+  os << "    const R& " << P << "_iU = " << iU << ";\n";
   auto Jpoly = [&](const std::vector<double> &coef) {
     std::vector<Poly> J(n);
     for (int a = 0; a < n; ++a)
@@ -591,8 +634,12 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
     Poly q = Up * coef[l];
     for (int a = 0; a < n; ++a) if (T.eta[l][a]) q = q - X[a];
     if (q.zero()) return "";
+    const std::string key = std::string(tag) + eta_key + vec_key(coef) + std::to_string(l);
+    auto it = E.cache.find(key);
+    if (it != E.cache.end()) return it->second;
     std::string v = P + "_" + tag + std::to_string(l);
     os << "    const R " << v << " = (" << q.horner() << ") * " << P << "_iU;\n";
+    E.cache[key] = v;
     return v;
   };
   for (int l = 0; l < g.n_elec(); ++l) {
@@ -600,12 +647,20 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
     K[l] = emitQ(T.kappa, Xk, l, "Kk");
   }
   // V = sum_{electrons without external momentum} z + Jp . adj . Jp / U
-  std::string V = P + "_V";
+  std::string V;
   {
-    Poly uv;
-    for (int l = 0; l < g.n_elec(); ++l) if (T.alpha[l] == 0.0) uv = uv + Up * Poly::var(l);
-    for (int a = 0; a < n; ++a) uv = uv + Jp[a] * Xp[a];
-    os << "    const R " << V << " = (" << uv.horner() << ") * " << P << "_iU;\n";
+    const std::string key = "V" + eta_key + vec_key(T.alpha);
+    auto it = E.cache.find(key);
+    if (it != E.cache.end()) V = it->second;
+    else {
+      V = P + "_V";
+      Poly uv;
+      for (int l = 0; l < g.n_elec(); ++l) if (T.alpha[l] == 0.0) uv = uv + Up * Poly::var(l);
+      for (int a = 0; a < n; ++a) uv = uv + Jp[a] * Xp[a];
+      os << "    const R " << V << " = (" << uv.horner() << ") * " << P << "_iU;\n";
+      os << "    const R " << V << "_inv = R(1.0) / " << V << ";\n";
+      E.cache[key] = V;
+    }
   }
   // (1 + A_l) and (1 - A_l), expanded symbolically: (U +- U A_l) / U
   std::map<std::pair<int, int>, std::string> onepm_cache;
@@ -613,12 +668,16 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
     auto key = std::make_pair(l, minus);
     auto it = onepm_cache.find(key);
     if (it != onepm_cache.end()) return it->second;
+    const std::string gkey = std::string(minus ? "Bm" : "Bp") + eta_key + vec_key(T.alpha) + std::to_string(l);
+    auto git = E.cache.find(gkey);
+    if (git != E.cache.end()) { onepm_cache[key] = git->second; return git->second; }
     Poly q = Up * T.alpha[l];
     for (int a = 0; a < n; ++a) if (T.eta[l][a]) q = q - Xp[a];
     Poly w = minus ? Up - q : Up + q;
     std::string v = P + (minus ? "_Bm" : "_Bp") + std::to_string(l);
     os << "    const R " << v << " = (" << w.horner() << ") * " << P << "_iU;\n";
     onepm_cache[key] = v;
+    E.cache[gkey] = v;
     return v;
   };
   // B_ij on demand
@@ -631,21 +690,29 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
     Poly bp;
     for (int a = 0; a < n; ++a) for (int b = 0; b < n; ++b)
       if (T.eta[i][a] && T.eta[j][b]) bp = bp + adjp[a][b];
-    std::string v = bp.zero() ? "" : P + "_B" + std::to_string(i) + "_" + std::to_string(j);
-    if (!bp.zero()) os << "    const R " << v << " = " << bp.horner() << ";\n";
+    std::string v;
+    if (!bp.zero()) {
+      const std::string gkey = "B" + eta_key + std::to_string(i) + "_" + std::to_string(j);
+      auto git = E.cache.find(gkey);
+      if (git != E.cache.end()) v = git->second;
+      else {
+        v = P + "_B" + std::to_string(i) + "_" + std::to_string(j);
+        os << "    const R " << v << " = " << bp.horner() << ";\n";
+        E.cache[gkey] = v;
+      }
+    }
     Bc[key] = v;
     return v;
   };
   // |A|, |C|, |K| in FP32 for the condition estimate (all lie in [-1, 1]
   // up to O(1) factors, so single precision has the range and accuracy an
   // estimate needs; FP32 is the cheap pipe)
-  std::map<std::string, std::string> fabs_cache;
   auto fabsvar = [&](const std::string &v) -> std::string {
-    auto it = fabs_cache.find(v);
-    if (it != fabs_cache.end()) return it->second;
+    auto it = E.cache.find("fa:" + v);
+    if (it != E.cache.end()) return it->second;
     std::string fv = "fa_" + v;
     os << "    const float " << fv << " = fabsf(float(to_double(" << v << ")));\n";
-    fabs_cache[v] = fv;
+    E.cache["fa:" + v] = fv;
     return fv;
   };
   // block values: recursive, returns (value, absolute-sum) variable names per k
@@ -713,18 +780,30 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
       for (auto &pr : pat) { int a = mom_items[pr.first], b = mom_items[pr.second]; D.pair_partner[a] = b; D.pair_partner[b] = a; }
       D.go(0, mono_identity(), -1, -1, 0u, -1);
       std::string poly, apoly;
+      Poly vpoly;                               // value polynomial over named factors
+      std::vector<std::string> vnames;
+      std::map<std::string, int> vid;
+      auto var_id = [&](const std::string &nm) {
+        auto it = vid.find(nm);
+        if (it != vid.end()) return it->second;
+        vid[nm] = int(vnames.size());
+        vnames.push_back(nm);
+        return int(vnames.size()) - 1;
+      };
       for (auto &kv : D.acc) {
         cd c = kv.second;
         if (std::abs(c.imag()) > 1e-9 * (1 + std::abs(c.real()))) { fprintf(stderr, "complex coefficient %g %g\n", c.real(), c.imag()); exit(1); }
         double cr = snap(c.real());
         if (cr == 0.0) continue;
         std::string mono, amono;
+        std::vector<int> mids;
         for (int f = 0; f < m; ++f)
           for (int pmn = 0; pmn < 2; ++pmn)
             if (kv.first.pmask >> (2 * f + pmn) & 1) {
               const std::string v = onepm(mom_line[f], pmn);
               mono += " * " + v;
               amono += " * " + fabsvar(v);
+              mids.push_back(var_id(v));
             }
         if (kv.first.deriv >= 0) {
           int f = kv.first.deriv;
@@ -732,14 +811,19 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
           if (v.empty()) continue;
           mono += " * " + v;
           amono += " * " + fabsvar(v);
+          mids.push_back(var_id(v));
         }
         poly += (poly.empty() ? "R(" : " + R(") + dstr(cr) + ")" + mono;
+        std::sort(mids.begin(), mids.end());
+        vpoly.t[mids] += cr;
         apoly += std::string(apoly.empty() ? "" : " + ") + dstr(std::abs(cr)) + "f" + amono;
         ++st.monos;
       }
       if (poly.empty()) continue;
       int k = int(pat.size());
       std::string var = P + "_b" + std::to_string(bi) + "k" + std::to_string(k);
+      vpoly.clean();
+      if (!vpoly.zero()) poly = vpoly.horner_named(vnames);
       std::string contrib = bprod.empty() ? "(" + poly + ")" : bprod + " * (" + poly + ")";
       std::string acontrib = bprod.empty() ? "double(" + apoly + ")" : "fabs(to_double(" + bprod + ")) * double(" + apoly + ")";
       std::string avar = var + "_a";
@@ -775,7 +859,7 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
   auto &vals = va.first;
   auto &avals = va.second;
   // combine: (-1)^n 4^-n sum_k (-1)^k Gamma(n-k) U^-2 V^(k-n) (2U)^-k val_k
-  os << "    const R " << P << "_iV = R(1.0) / " << V << ";\n";
+  os << "    const R& " << P << "_iV = " << V << "_inv;\n";
   std::string acc, aacc;
   for (int k = 0; k < n && k < int(vals.size()); ++k) {
     if (vals[k].empty()) continue;
@@ -827,11 +911,19 @@ int main(int argc, char **argv) {
       // algorithmic FP64 operations of the integrand: binary operators in the
       // emitted expressions plus the absum accumulation and the final sum
       {
-        const std::string body = E.os.str();
+        // FP64 operations only: the condition-estimate lines (float and
+        // double accumulators of absolute values) run on other pipes or are
+        // not part of the value
+        std::istringstream lines(E.os.str());
+        std::string ln;
         long ops = 0;
-        for (size_t k = 0; k + 2 < body.size(); ++k)
-          if (body[k] == ' ' && body[k + 2] == ' ' && (body[k + 1] == '+' || body[k + 1] == '-' || body[k + 1] == '*' || body[k + 1] == '/')) ++ops;
-        ops += 3 * long(outs.size());
+        while (std::getline(lines, ln)) {
+          if (ln.find("float ") != std::string::npos || ln.find("double ") != std::string::npos ||
+              ln.find("_a = ") != std::string::npos || ln.find("_abs") != std::string::npos) continue;
+          for (size_t k = 0; k + 2 < ln.size(); ++k)
+            if (ln[k] == ' ' && ln[k + 2] == ' ' && (ln[k + 1] == '+' || ln[k + 1] == '-' || ln[k + 1] == '*' || ln[k + 1] == '/')) ++ops;
+        }
+        ops += long(outs.size());   // the final sum of the terms
         reg_flops.push_back(ops);
       }
       std::ofstream f(dir + "/g_" + std::to_string(id) + ".cuh");

@@ -265,6 +265,7 @@ extern "C" int qed_gauge_class(const qed_graph *in, int kmn[3]) {
 }
 
 extern "C" int qed_diagram_free(qed_diag *d);
+extern "C" int qed_eval_points(qed_diag *d, const double *z_dev, uint64_t n, int prec, double *f_dev);
 extern "C" int qed_diagram_load(qed_ctx *ctx, const qed_graph *gin, const qed_pdf *pdf, qed_diag **out) {
   if (!ctx || !out) return set_err(QED_EINVAL, "ctx/out is NULL");
   qed::Graph g;
@@ -787,3 +788,68 @@ extern "C" int qed_pdf_grad(qed_diag *d, uint64_t begin, uint64_t n, uint64_t se
   *m2 = M2;
   return QED_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Calibrated Deg: the growth exponent of the integrand in the limit where the
+// lines of s shrink (z_s -> eps z_s), measured on the GPU in double-double,
+// caps Deg(s) at |s| - a_s, the value at which w = f / p stays bounded in
+// that limit.  Deg(s) = max(d_min, min(rule(s), |s| - a_s)).
+// ---------------------------------------------------------------------------
+extern "C" int qed_diagram_calibrate_deg(qed_diag *d, int n_base, uint64_t seed) {
+  if (!d || n_base < 1 || n_base > 64) return set_err(QED_EINVAL, "n_base must be in [1, 64]");
+  qed_ctx *c = d->ctx;
+  const int N = d->N;
+  const size_t M = size_t(1) << N;
+  const double e1 = 1e-4, e2 = 1e-6;
+  // base points: uniform on the simplex (normalised exponentials)
+  uint64_t st = seed * 0x9E3779B97F4A7C15ull + 0x2545F4914F6CDD1Dull;
+  auto next = [&]() { st ^= st << 13; st ^= st >> 7; st ^= st << 17; return (double((st >> 11) + 1) * 1.1102230246251565e-16); };
+  std::vector<double> base(size_t(n_base) * N);
+  for (int b = 0; b < n_base; ++b) {
+    double sum = 0.0;
+    for (int l = 0; l < N; ++l) { base[b * N + l] = -std::log(next()); sum += base[b * N + l]; }
+    for (int l = 0; l < N; ++l) base[b * N + l] /= sum;
+  }
+  const size_t npts = (M - 2) * size_t(n_base) * 2;
+  std::vector<double> pts(npts * N), f(npts);
+  size_t k = 0;
+  for (size_t m = 1; m + 1 < M; ++m)
+    for (int b = 0; b < n_base; ++b)
+      for (double e : {e1, e2}) {
+        for (int l = 0; l < N; ++l) pts[k * N + l] = base[b * N + l] * ((m >> l & 1) ? e : 1.0);
+        ++k;
+      }
+  CUDA_TRY(cudaSetDevice(c->device));
+  double *dz = nullptr, *df = nullptr;
+  CUDA_TRY(cudaMalloc(&dz, pts.size() * sizeof(double)));
+  if (cudaMalloc(&df, f.size() * sizeof(double)) != cudaSuccess) { cudaFree(dz); return set_err(QED_ENOMEM, "calibration buffers"); }
+  int rc = QED_OK;
+  if (cudaMemcpy(dz, pts.data(), pts.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) rc = set_err(QED_ECUDA, "copy");
+  if (!rc) rc = qed_eval_points(d, dz, npts, 1, df);
+  if (!rc && cudaMemcpy(f.data(), df, f.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) rc = set_err(QED_ECUDA, "copy back");
+  cudaFree(dz);
+  cudaFree(df);
+  if (rc) return rc;
+  k = 0;
+  for (size_t m = 1; m + 1 < M; ++m) {
+    double a = -1e300;
+    for (int b = 0; b < n_base; ++b) {
+      const double f1 = std::fabs(f[k]), f2 = std::fabs(f[k + 1]);
+      k += 2;
+      if (f1 > 0.0 && f2 > 0.0 && std::isfinite(f1) && std::isfinite(f2))
+        a = std::max(a, std::log(f2 / f1) / std::log(e1 / e2));
+    }
+    if (a > -1e299) {
+      const double cap = double(__builtin_popcountll(m)) - a;
+      d->deg0[m] = std::max(d->d_min, std::min(d->deg0[m], cap));
+    }
+  }
+  return rebuild_tables(d);
+}
+
+extern "C" int qed_diagram_get_deg(const qed_diag *d, double *deg_out) {
+  if (!d || !deg_out) return set_err(QED_EINVAL, "NULL argument");
+  for (size_t m = 0; m < d->deg.size(); ++m) deg_out[m] = d->deg[m];
+  return QED_OK;
+}
+

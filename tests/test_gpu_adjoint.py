@@ -68,3 +68,24 @@ def test_tuning_lowers_second_moment_unbiased(ctx):
     after = d.integrate(1 << 24, seed=21)
     assert after.variance < before.variance
     assert abs(after.value - before.value) < 4 * math.sqrt(after.variance + before.variance)
+
+
+def test_calibrated_deg_caps_rule_and_matches_oracle_sampler(ctx):
+    """Calibrated Deg: never above the rule, positive, and the oracle samples
+    the same points from the table read back from the library."""
+    from oracle.pdf import f_table, sample_points
+    g = q.enumerate_graphs(2)[3]
+    og = o_enum(2)[3]
+    d = ctx.load(g)
+    rule = d.deg_table()
+    d.calibrate_deg(n_base=8, seed=1)
+    cal = d.deg_table()
+    N = og.n_lines
+    assert all(0 < cal[m] <= rule[m] + 1e-15 for m in range(1, (1 << N) - 1))
+    # the complement of the self-energy subgraph (lines 0, 1, 3, 4) is lowered
+    assert cal[0b011011] < rule[0b011011]
+    z, f, lp, fl = d.dump_points(0, 500, seed=4)
+    u = uniforms(np.arange(500), g.stream_id, 4, 2 * (N - 1))
+    x, lpo, _ = sample_points(u, cal, f_table(cal, N), N)
+    np.testing.assert_allclose(z.cpu().numpy(), x, rtol=1e-12)
+    np.testing.assert_allclose(lp.cpu().numpy(), lpo, rtol=1e-12, atol=1e-12)
