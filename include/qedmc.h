@@ -201,6 +201,25 @@ int qed_diagram_flops(const qed_diag *d, double *flops_per_sample);
  * FMA): every SM runs independent FMA chains for about `ms` milliseconds. */
 int qed_fp64_peak(int device, double ms, double *flops_per_s);
 
+/* ---- integration without allocation -------------------------------------
+ * No counterpart in the paper.  Same estimate as qed_integrate_range (equal
+ * within rounding: the block partials are folded on the device), for callers
+ * that must not allocate device memory once they are running -- an
+ * application whose own pool allocator owns all device memory and forbids
+ * further cudaMalloc, or a latency-critical loop where an allocation, which
+ * can synchronise the device, is not acceptable.  The call allocates nothing
+ * on the device or the host: its scratch is one file-scope device array of
+ * about 650 KB that every GPU loading the library holds until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (with the device current); make that first call before any stream capture.
+ * Limits: at most 2048 blocks in the context's launch shape (QED_EINVAL
+ * otherwise); more than 65536 flagged points in a chunk of 2^30 samples are
+ * found again by re-scanning the chunk instead of being queued.  All calls in
+ * the process share the array, so calls that overlap on the GPU (other
+ * threads, other streams) race: serialise them.  Each call clears the
+ * counters it needs before use. */
+int qed_integrate_range_noalloc(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed, qed_result *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -853,3 +853,122 @@ extern "C" int qed_diagram_get_deg(const qed_diag *d, double *deg_out) {
   return QED_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Integration without allocation (no counterpart in the paper).
+//
+// For callers that must not allocate device memory once they are running:
+// for example an application that has handed all device memory to its own
+// pool allocator and forbids further cudaMalloc, or a latency-critical loop
+// where an allocation (which can synchronise the device) is not acceptable.
+// The scratch of the FP64 integration kernel (block partials, the flagged
+// queue and its counter) lives in one file-scope device array instead of
+// context buffers, and the block partials are folded on the device, so the
+// call allocates nothing on the device or the host.
+// ---------------------------------------------------------------------------
+#define QED_NOALLOC_MAX_BLOCKS 2048
+#define QED_NOALLOC_QUEUE 65536
+struct NoAllocScratch {
+  double part[2][QED_NOALLOC_MAX_BLOCKS][4];              // FP64 pass, double-double pass
+  unsigned long long cnt[2][QED_NOALLOC_MAX_BLOCKS][2];
+  unsigned long long queue[QED_NOALLOC_QUEUE];
+  double result[8];                                       // folded sums (see k_noalloc_fold)
+  unsigned int queue_len;
+};
+// Every GPU that loads the library holds this array (about 650 KB) until exit.
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+// Folds the per-block partials of both passes in block order, in
+// double-double: result = {sum w (hi, lo), sum w^2 (hi, lo), flagged, unstable}.
+__global__ void k_noalloc_fold(NoAllocScratch *s, int blocks, int with_dd) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  dd x{0.0, 0.0}, y{0.0, 0.0};
+  unsigned long long nf = 0, nu = 0;
+  for (int p = 0; p < (with_dd ? 2 : 1); ++p)
+    for (int b = 0; b < blocks; ++b) {
+      x = x + dd{s->part[p][b][0], s->part[p][b][1]};
+      y = y + dd{s->part[p][b][2], s->part[p][b][3]};
+      nf += s->cnt[p][b][0];
+      nu += s->cnt[p][b][1];
+    }
+  s->result[0] = x.hi; s->result[1] = x.lo; s->result[2] = y.hi; s->result[3] = y.lo;
+  s->result[4] = double(nf); s->result[5] = double(nu);
+}
+
+static std::mutex g_noalloc_mu;
+static NoAllocScratch *g_noalloc_ptr[64] = {nullptr};
+
+// The array's device address on the current device (looked up once per
+// device with that device current; the host-side name is only a stand-in).
+static int noalloc_scratch(int device, NoAllocScratch **out) {
+  if (device < 0 || device >= 64) return set_err(QED_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return set_err(QED_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_ptr[device] = static_cast<NoAllocScratch *>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return QED_OK;
+}
+
+extern "C" int qed_integrate_range_noalloc(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed, qed_result *out) {
+  if (!d || !out) return set_err(QED_EINVAL, "diag/out is NULL");
+  qed_ctx *c = d->ctx;
+  const int threads = c->threads;
+  const int blocks = c->blocks > 0 ? c->blocks : 4 * c->sms;
+  if (blocks > QED_NOALLOC_MAX_BLOCKS)
+    return set_err(QED_EINVAL, "qed_integrate_range_noalloc: at most 2048 blocks (qed_ctx_set_launch)");
+  CUDA_TRY(cudaSetDevice(c->device));
+  NoAllocScratch *S = nullptr;
+  int rc = noalloc_scratch(c->device, &S);
+  if (rc) return rc;
+  const KernelSet &K = *g_kernels[d->fid];
+  const size_t smem = table_smem(d->N);
+  qed_result r;
+  std::memset(&r, 0, sizeof r);
+  r.n = n;
+  CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+  const uint64_t chunk = uint64_t(1) << 30;
+  for (uint64_t off = 0; off < n; off += chunk) {
+    const uint64_t m = std::min(chunk, n - off);
+    KParams P = base_params(d, begin + off, m, seed);
+    P.partials = &S->part[0][0][0]; P.counts = &S->cnt[0][0][0];
+    P.queue = S->queue; P.queue_len = &S->queue_len; P.queue_cap = QED_NOALLOC_QUEUE;
+    CUDA_TRY(cudaMemsetAsync(&S->queue_len, 0, sizeof(unsigned int), c->stream));
+    void *args[] = {&P};
+    if ((rc = launch(K.integrate, blocks, threads, smem, c->stream, args))) return rc;
+    ++r.launches;
+    unsigned int qn = 0;
+    CUDA_TRY(cudaMemcpyAsync(&qn, &S->queue_len, sizeof qn, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    int with_dd = 0;
+    if (qn > 0) {
+      int mode = qn > QED_NOALLOC_QUEUE ? 1 : 0;   // overflow: re-scan the range, no extra storage
+      unsigned int qcount = std::min<unsigned int>(qn, QED_NOALLOC_QUEUE);
+      KParams P2 = P;
+      P2.partials = &S->part[1][0][0]; P2.counts = &S->cnt[1][0][0];
+      void *args2[] = {&P2, &mode, &qcount};
+      if ((rc = launch(K.redo, blocks, threads, smem, c->stream, args2))) return rc;
+      ++r.launches;
+      with_dd = 1;
+    }
+    void *args3[] = {&S, (void *)&blocks, &with_dd};
+    if ((rc = launch((const void *)k_noalloc_fold, 1, 32, 0, c->stream, args3))) return rc;
+    double res[6];
+    CUDA_TRY(cudaMemcpyAsync(res, S->result, sizeof res, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    dd_acc(r.sum_w[0], r.sum_w[1], res[0], res[1]);
+    dd_acc(r.sum_w2[0], r.sum_w2[1], res[2], res[3]);
+    r.n_flagged += (unsigned long long)res[4];
+    r.n_unstable += (unsigned long long)res[5];
+  }
+  CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+  CUDA_TRY(cudaEventSynchronize(c->ev1));
+  float ms = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  r.seconds = ms * 1e-3;
+  finish(&r);
+  *out = r;
+  return QED_OK;
+}
