@@ -646,19 +646,26 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
   CUDA_TRY(cudaEventRecord(c->ev0, st));
   for (int r = 0; r < rounds; ++r) {
     // split n_items among graphs: round 0 (and policy 1) equal, else by weight
-    std::vector<unsigned int> cnt(k, 0);
+    // one item per graph, the rest by weight (largest-remainder rounding)
+    std::vector<unsigned int> cnt(k, 1);
+    std::vector<double> frac(k, 0.0);
     double wsum = 0.0;
     for (int g = 0; g < k; ++g) wsum += (r == 0 || o.policy == 1) ? 1.0 : weight[g];
-    unsigned int given = 0;
+    unsigned int given = unsigned(k);
     for (int g = 0; g < k; ++g) {
       const double w = (r == 0 || o.policy == 1) ? 1.0 : weight[g];
-      cnt[g] = std::max(1u, unsigned(std::floor(double(n_items - k) * w / wsum)) + 1u);
-      given += cnt[g];
+      const double q = double(n_items - k) * w / wsum;
+      const unsigned int fl = unsigned(std::floor(q));
+      cnt[g] += fl;
+      frac[g] = q - double(fl);
+      given += fl;
     }
-    // hand out any remainder round-robin by weight order, trim any excess
-    int gi = 0;
-    while (given < n_items) { ++cnt[gi % k]; ++given; ++gi; }
-    while (given > n_items) { int gm = int(std::max_element(cnt.begin(), cnt.end()) - cnt.begin()); --cnt[gm]; --given; }
+    while (given < n_items) {
+      const int gm = int(std::max_element(frac.begin(), frac.end()) - frac.begin());
+      ++cnt[gm];
+      frac[gm] = -1.0;
+      ++given;
+    }
     unsigned int it = 0;
     for (int g = 0; g < k; ++g)
       for (unsigned int j = 0; j < cnt[g]; ++j) {

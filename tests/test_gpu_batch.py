@@ -41,7 +41,7 @@ def test_batch_equals_per_graph_on_same_counters(setup, policy, use_graph, list_
 
 def test_batch_variance_policy_moves_samples_to_noisy_graphs(setup):
     ctx, ds = setup
-    res = ctx.integrate_batch(ds, 64 * (1 << 18), seed=5, policy="variance", rounds=4, chunk=1 << 18)
+    res = ctx.integrate_batch(ds, 512 * (1 << 15), seed=5, policy="variance", rounds=4, chunk=1 << 15)
     per_sample_sigma = [math.sqrt(r.variance * r.n) for r in res]
     # the noisiest graph gets more samples than the quietest one
     hi = max(range(6), key=lambda i: per_sample_sigma[i])
