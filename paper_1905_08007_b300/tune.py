@@ -69,14 +69,14 @@ def tune(diag, steps=20, n=1 << 22, lr=0.05, seed=1234, log=None):
         opt.zero_grad()
         m2 = SecondMoment.apply(alpha, beta, diag, n, seed, (s + 1) * n)
         m2.backward()
-        hist.append(float(m2))
-        if float(m2) < best[0]:
-            best = (float(m2), alpha.detach().clone(), beta.detach().clone())
+        hist.append(m2.item())
+        if m2.item() < best[0]:
+            best = (m2.item(), alpha.detach().clone(), beta.detach().clone())
         opt.step()
         with torch.no_grad():
             alpha.clamp_(-0.45, 2.0)
             beta.clamp_(-3.0, 3.0)
         if log:
-            log(s, float(m2))
+            log(s, m2.item())
     _set_params(diag, best[1].tolist(), best[2].tolist())
     return best[1], best[2], hist
