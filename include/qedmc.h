@@ -174,6 +174,7 @@ typedef struct {
   uint64_t chunk;      /* samples per work item (default 262144, <= 2^31) */
   int use_graph;       /* 0 = default: capture one round as a CUDA graph and replay it; -1 = plain launches */
   int list_div;        /* flagged-list capacity per item = chunk / list_div (default 16) */
+  uint64_t counter_base; /* first Philox counter of every graph's samples (default 0) */
 } qed_batch_opts;
 
 /* Integrate the k graphs d[0..k-1] (all loaded on the same context) with

@@ -38,7 +38,7 @@ class _Pdf(C.Structure):
 
 class _BatchOpts(C.Structure):
     _fields_ = [("policy", C.c_int), ("rounds", C.c_int), ("chunk", C.c_uint64), ("use_graph", C.c_int),
-                ("list_div", C.c_int)]
+                ("list_div", C.c_int), ("counter_base", C.c_uint64)]
 
 
 class _Result(C.Structure):
@@ -219,12 +219,14 @@ class Context:
         return Diagram(self, g, deg, c_div, d_min)
 
     def integrate_batch(self, diagrams, total_samples: int, seed: int = 0, policy: str = "variance",
-                        rounds: int = 4, chunk: int = 1 << 18, use_graph: bool = True, list_div: int = 16):
+                        rounds: int = 4, chunk: int = 1 << 18, use_graph: bool = True, list_div: int = 16,
+                        counter_base: int = 0):
         """qed_integrate_batch: all graphs in one persistent launch per round,
         samples shared by running variance (policy "variance") or equally."""
         k = len(diagrams)
         arr = (C.c_void_p * k)(*[d._h.value for d in diagrams])
-        o = _BatchOpts(0 if policy == "variance" else 1, rounds, chunk, 0 if use_graph else -1, list_div)
+        o = _BatchOpts(0 if policy == "variance" else 1, rounds, chunk, 0 if use_graph else -1, list_div,
+                       counter_base)
         out = (_Result * k)()
         _check(load_library().qed_integrate_batch(self._h, arr, k, int(total_samples), seed, C.byref(o), out))
         return [Result._from_c(out[i]) for i in range(k)]
