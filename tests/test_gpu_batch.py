@@ -55,3 +55,13 @@ def test_batch_is_deterministic(setup):
     a = ctx.integrate_batch(ds, 12 * (1 << 18), seed=6, rounds=2)
     b = ctx.integrate_batch(ds, 12 * (1 << 18), seed=6, rounds=2)
     assert [r.sum_w for r in a] == [r.sum_w for r in b]
+
+
+def test_autotuner_picks_a_measured_shape(setup):
+    from paper_1905_08007_b300.autotune import tune_batch_chunk, tune_launch
+    ctx, ds = setup
+    best, table = tune_launch(ctx, ds[0], samples=1 << 22, threads=(128, 256), blocks_per_sm=(2, 4))
+    assert best["samples_per_s"] == max(t["samples_per_s"] for t in table)
+    ctx.set_launch(256, 0)
+    bc, tb = tune_batch_chunk(ctx, ds, samples=1 << 24, chunks=(1 << 16, 1 << 18))
+    assert bc["samples_per_s"] == max(t["samples_per_s"] for t in tb)
