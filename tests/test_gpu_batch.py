@@ -65,3 +65,15 @@ def test_autotuner_picks_a_measured_shape(setup):
     ctx.set_launch(256, 0)
     bc, tb = tune_batch_chunk(ctx, ds, samples=1 << 24, chunks=(1 << 16, 1 << 18))
     assert bc["samples_per_s"] == max(t["samples_per_s"] for t in tb)
+
+
+def test_batch_times_its_kernel_and_leaves_no_cuda_error(setup):
+    """The persistent kernel's time is reported, and a torch kernel launched
+    right after a batched call (graph replay) sees no stale CUDA error."""
+    ctx, ds = setup
+    res = ctx.integrate_batch(ds, 12 * (1 << 18), seed=8, rounds=2)
+    assert 0.0 < res[0].kernel_seconds <= res[0].seconds
+    x = torch.zeros(1 << 20, device="cuda")
+    x.add_(1.0)
+    torch.cuda.synchronize()
+    assert float(x.sum()) == float(1 << 20)
