@@ -880,6 +880,8 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
 
 int main(int argc, char **argv) {
   if (argc < 3) { fprintf(stderr, "usage: qed_gen out_dir n1 [n2 ...]\n"); return 2; }
+  int split_from = 3;
+  if (const char *e = getenv("QED_GEN_SPLIT_FROM")) split_from = atoi(e);
   init_gammas();
   init_projectors();
   const std::string dir = argv[1];
@@ -899,12 +901,38 @@ int main(int argc, char **argv) {
     for (size_t gi = 0; gi < gs.size(); ++gi) {
       const Graph &g = gs[gi];
       auto terms = build_terms(g);
+      // From loop order `split_from` on, each forest term becomes its own
+      // non-inlined device function (compile time grows faster than the
+      // size of one straight-line function); below it the terms share one
+      // function and its polynomials.
+      const bool split = g.n >= split_from;
       Emitter E;
       std::vector<std::string> outs;
+      std::ostringstream term_funcs;
+      long split_ops = 0;
       for (auto &t : terms) {
         TermInfo T = analyse(g, t);
         std::string o = "term" + std::to_string(outs.size());
-        emit_term(E, T, o, st);
+        if (!split) {
+          emit_term(E, T, o, st);
+        } else {
+          Emitter Et;
+          emit_term(Et, T, "v", st);
+          const std::string fn = "qed_t_" + g.name() + "_" + std::to_string(outs.size());
+          term_funcs << "template <class R>\n__device__ __noinline__ R " << fn
+                     << "(const R* __restrict__ z, double& tabs) {\n" << Et.os.str()
+                     << "    tabs = v_abs;\n    return v;\n}\n\n";
+          E.os << "    double " << o << "_abs;\n";
+          E.os << "    const R " << o << " = " << fn << "<R>(z, " << o << "_abs);\n";
+          std::istringstream lines(Et.os.str());
+          std::string ln;
+          while (std::getline(lines, ln)) {
+            if (ln.find("float ") != std::string::npos || ln.find("double ") != std::string::npos ||
+                ln.find("_a = ") != std::string::npos || ln.find("_abs") != std::string::npos) continue;
+            for (size_t k = 0; k + 2 < ln.size(); ++k)
+              if (ln[k] == ' ' && ln[k + 2] == ' ' && (ln[k + 1] == '+' || ln[k + 1] == '-' || ln[k + 1] == '*' || ln[k + 1] == '/')) ++split_ops;
+          }
+        }
         outs.push_back(o);
       }
       const int id = int(reg.size());
@@ -923,12 +951,13 @@ int main(int argc, char **argv) {
           for (size_t k = 0; k + 2 < ln.size(); ++k)
             if (ln[k] == ' ' && ln[k + 2] == ' ' && (ln[k + 1] == '+' || ln[k + 1] == '-' || ln[k + 1] == '*' || ln[k + 1] == '/')) ++ops;
         }
-        ops += long(outs.size());   // the final sum of the terms
+        ops += long(outs.size()) + split_ops;   // the final sum of the terms
         reg_flops.push_back(ops);
       }
       std::ofstream f(dir + "/g_" + std::to_string(id) + ".cuh");
       f << banner << "#pragma once\n\n";
       f << "// " << g.name() << ": " << terms.size() << " forest terms\n";
+      f << term_funcs.str();
       f << "template <class R>\n__device__ __forceinline__ R qed_f_" << g.name() << "(const R* __restrict__ z, double& absum) {\n";
       f << E.os.str();
       f << "    absum = 0.0;\n";

@@ -609,15 +609,16 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
   double *o_pdd = o_part + 4 * size_t(n_items);
   unsigned long long *o_cnt = (unsigned long long *)(o_pdd + 4 * size_t(n_items));
   unsigned long long *o_cdd = o_cnt + 2 * size_t(n_items);
-  auto enqueue_round = [&](cudaStream_t st) -> int {
+  auto enqueue_round = [&](cudaStream_t st, bool capturing) -> int {
     CUDA_TRY(cudaMemcpyAsync(dd_items.p, h_items.p, sizeof(BatchItem) * n_items, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemsetAsync(dd_next.p, 0, sizeof(unsigned int), st));
     void *args[] = {&B};
     // external event-record nodes when captured, so the kernel can be timed
     // after every replay
-    CUDA_TRY(cudaEventRecordWithFlags(c->evk0, st, cudaEventRecordExternal));
+    const unsigned int evflags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    CUDA_TRY(cudaEventRecordWithFlags(c->evk0, st, evflags));
     CUDA_TRY(cudaLaunchKernel(qed_batch_kernels[0], dim3(grid1), dim3(256), args, smem, st));
-    CUDA_TRY(cudaEventRecordWithFlags(c->evk1, st, cudaEventRecordExternal));
+    CUDA_TRY(cudaEventRecordWithFlags(c->evk1, st, evflags));
     CUDA_TRY(cudaLaunchKernel(qed_batch_kernels[1], dim3(grid2), dim3(256), args, smem, st));
     CUDA_TRY(cudaMemcpyAsync(o_part, dd_part.p, sizeof(double) * 4 * n_items, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(o_pdd, dd_pdd.p, sizeof(double) * 4 * n_items, cudaMemcpyDeviceToHost, st));
@@ -632,7 +633,7 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
     if (st == 0) { CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own_stream = true; }
     cudaGraph_t graph;
     CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_round(st);
+    int rc = enqueue_round(st, true);
     cudaError_t ce = cudaStreamEndCapture(st, &graph);
     if (rc) return rc;
     if (ce != cudaSuccess) return set_err(QED_ECUDA, std::string("capture: ") + cudaGetErrorString(ce));
@@ -679,7 +680,7 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
         ++it;
       }
     if (gexec) { CUDA_TRY(cudaGraphLaunch(gexec, st)); }
-    else { int rc = enqueue_round(st); if (rc) return rc; }
+    else { int rc = enqueue_round(st, false); if (rc) return rc; }
     launches += 2;
     CUDA_TRY(cudaStreamSynchronize(st));
     {
