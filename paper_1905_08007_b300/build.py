@@ -74,18 +74,44 @@ def build(orders=DEFAULT_ORDERS, force=False, verbose_ptxas=False, jobs=None):
     objdir.mkdir(exist_ok=True)
     for old in objdir.glob("*.o"):
         old.unlink()
+    big = [(gid, ln) for gid, ln in ids if int(ln) >= 9]      # three loops and up
+    rdc = bool(big)
     base = [_nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
             "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC, "-I", GEN]
+    if rdc:
+        base.append("-rdc=true")
     if verbose_ptxas:
         base.append("-Xptxas=-v")
     units = []
+    bigset = {gid for gid, _ in big}
     for gid, lines in ids:
         tu = GEN / f"k_{gid}.cu"
-        tu.write_text(f'#include "qed_kernels.cuh"\n#include "g_{gid}.cuh"\nQED_DEFINE_KSET({gid}, {lines})\n')
+        text = f'#include "qed_kernels.cuh"\n#include "g_{gid}.cuh"\nQED_DEFINE_KSET({gid}, {lines})\n'
+        if gid in bigset:
+            # the integrand once per precision, for the batched kernels to link against
+            text += (f"__device__ double qed_ext_f64_{gid}(const double* z, double& a) "
+                     f"{{ return qed_gen_f<{gid}>::template eval<double>(z, a); }}\n"
+                     f"__device__ dd qed_ext_dd_{gid}(const dd* z, double& a) "
+                     f"{{ return qed_gen_f<{gid}>::template eval<dd>(z, a); }}\n")
+        tu.write_text(text)
         units.append((tu, objdir / f"k_{gid}.o"))
-    # the persistent batched kernels: one switch over every generated graph
+    # the persistent batched kernels: one switch over every generated graph;
+    # graphs of three loops and up are linked in (relocatable device code)
+    # rather than compiled again here
     btu = GEN / "k_batch.cu"
-    inc = "".join(f'#include "g_{gid}.cuh"\n' for gid, _ in ids)
+    inc = ""
+    for gid, _ in ids:
+        if gid not in bigset:
+            inc += f'#include "g_{gid}.cuh"\n'
+        else:
+            inc += (f"extern __device__ double qed_ext_f64_{gid}(const double*, double&);\n"
+                    f"extern __device__ dd qed_ext_dd_{gid}(const dd*, double&);\n"
+                    f"template <> struct qed_gen_f<{gid}> {{\n"
+                    f"  template <class R> __device__ static R eval(const R* z, double& a);\n}};\n"
+                    f"template <> template <> __device__ double qed_gen_f<{gid}>::eval<double>(const double* z, double& a) "
+                    f"{{ return qed_ext_f64_{gid}(z, a); }}\n"
+                    f"template <> template <> __device__ dd qed_gen_f<{gid}>::eval<dd>(const dd* z, double& a) "
+                    f"{{ return qed_ext_dd_{gid}(z, a); }}\n")
     c64 = " ".join(f"case {gid}: batch_item_fp64<{gid}, {ln}>(B, it, I, smem); break;" for gid, ln in ids)
     cdd = " ".join(f"case {gid}: batch_item_dd<{gid}, {ln}>(B, it, I, smem); break;" for gid, ln in ids)
     btu.write_text(
@@ -111,7 +137,8 @@ def build(orders=DEFAULT_ORDERS, force=False, verbose_ptxas=False, jobs=None):
         for src, err in ex.map(compile_one, units):
             if verbose_ptxas and err:
                 print(f"== {src.name}\n{err}")
-    _run([_nvcc(), ARCH, "-shared", "-o", LIB] + [o for _, o in units] + ["-lcudart"])
+    _run([_nvcc(), ARCH, "-shared"] + (["-rdc=true"] if rdc else []) + ["-o", LIB] +
+         [o for _, o in units] + ["-lcudart"])
     stamp.write_text(key)
     return LIB
 
