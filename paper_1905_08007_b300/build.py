@@ -1,6 +1,6 @@
 """Build the native library in-tree: run the integrand generator, then nvcc.
 
-    python -m paper_1905_08007_b300.build [--orders 1 2] [--jobs 8]
+    python -m paper_1905_08007_b300.build [--orders 1 2 3] [--jobs 8]
 
 Steps:
 1. compile ``csrc/qed_gen.cpp`` with g++ and run it for the requested loop
@@ -29,7 +29,7 @@ ROOT = PKG.parent
 INCLUDE = ROOT / "include"
 BUILD = ROOT / "_build"
 LIB = PKG / "libqedmc.so"
-DEFAULT_ORDERS = (1, 2)
+DEFAULT_ORDERS = (1, 2, 3)
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

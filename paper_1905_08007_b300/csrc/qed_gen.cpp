@@ -42,7 +42,7 @@
 
 #include "qed_graph.hpp"
 
-using cd = std::complex<double>;
+using cd = std::complex<long double>;
 using namespace qed;
 
 // ---------------------------------------------------------------------------
@@ -105,7 +105,7 @@ static void init_projectors() {
   Dense one, g0, Pp, Sig[4], gj[4];
   for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) one[r][c] = (r == c) ? 1.0 : 0.0;
   to_dense(GAM[0], g0);
-  for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) { Pp[r][c] = 0.5 * (one[r][c] + g0[r][c]); W_F1[r][c] = 0.25 * (one[r][c] + g0[r][c]); }
+  for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) { Pp[r][c] = 0.5L * (one[r][c] + g0[r][c]); W_F1[r][c] = 0.25L * (one[r][c] + g0[r][c]); }
   for (int j = 1; j < 4; ++j) to_dense(GAM[j], gj[j]);
   // Sigma^l = (i/2) eps_ljk gamma^j gamma^k = diag(s_l, s_l)
   for (int l = 1; l < 4; ++l) {
@@ -113,7 +113,7 @@ static void init_projectors() {
     Dense a, b;
     dense_mul(gj[j], gj[k], a);
     dense_mul(gj[k], gj[j], b);
-    for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) Sig[l][r][c] = 0.5 * I * (a[r][c] - b[r][c]);
+    for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) Sig[l][r][c] = 0.5L * I * (a[r][c] - b[r][c]);
   }
   auto eps = [](int i, int j, int l) -> double {
     if (i == j || j == l || i == l) return 0.0;
@@ -137,15 +137,15 @@ static void init_projectors() {
         dense_mul(PS, gj[j], PSg);
         dense_mul(gj[j], PS, gPS);
         for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) {
-          W_MAG_H[i][j][r][c] += (I / 6.0) * e * PS[r][c];
+          W_MAG_H[i][j][r][c] += (I / 6.0L) * (long double)e * PS[r][c];
           // Tr[PS (-(g M - M g)/4)] = -1/4 (Tr[PS g M] - Tr[g PS M])
-          W_MAG_G[i][r][c] += (I / 6.0) * e * (-0.25) * (PSg[r][c] - gPS[r][c]);
+          W_MAG_G[i][r][c] += (I / 6.0L) * (long double)e * (-0.25L) * (PSg[r][c] - gPS[r][c]);
         }
       }
   for (int mu = 0; mu < 4; ++mu) {
     Dense d; to_dense(GAM_LOW[mu], d);
     Dense u; to_dense(GAM[mu], u);
-    for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) { W_UV[mu][r][c] = d[r][c] / 16.0; W_WF[mu][r][c] = u[r][c] / 16.0; }
+    for (int r = 0; r < 4; ++r) for (int c = 0; c < 4; ++c) { W_UV[mu][r][c] = d[r][c] / 16.0L; W_WF[mu][r][c] = u[r][c] / 16.0L; }
   }
 }
 
@@ -358,6 +358,7 @@ struct DFS {
   std::vector<int> pair_partner;          // item -> partner item for contracted / photon pairs, -1
   std::vector<int> pair_alpha;            // chosen alpha per item (filled in DFS)
   std::map<MonoKey, cd> acc;
+  std::map<MonoKey, long double> mag;
   int nitems;
 
   void leaf(const Mono &M, int mu, int dj, uint32_t pm, int dv) {
@@ -372,7 +373,7 @@ struct DFS {
       case PR_SEMASS: if (dv < 0) v = tr_wm(W_F1, M); break;
       case PR_SEWF: if (dv >= 0) v = tr_wm(W_WF[dj], M); break;
     }
-    if (std::abs(v) > 0) acc[MonoKey{pm, dv}] += v;
+    if (std::abs(v) > 0) { acc[MonoKey{pm, dv}] += v; mag[MonoKey{pm, dv}] += std::abs(v); }
   }
   // t: current item, M: product of items < t (rightmost first), mu/dj state
   void go(int t, const Mono &M, int mu, int dj, uint32_t pm, int dv) {
@@ -439,12 +440,14 @@ static std::string dstr(double x) {
 }
 
 // Dirac coefficients are rationals whose denominators divide 2^12 * 3;
-// summing them in floating point leaves last-bit noise, removed here.
-static double snap(double c) {
-  const double den = 4096.0 * 3.0;
-  double r = std::round(c * den);
-  if (std::abs(c * den - r) < 1e-6) return r / den;
-  fprintf(stderr, "coefficient %.17g is not a small rational\n", c);
+// summing them (in long double) leaves rounding noise relative to the
+// magnitude of the summed contributions, removed here.
+static double snap(long double c, long double mag) {
+  const long double den = 4096.0L * 3.0L;
+  const long double r = std::round(c * den);
+  const long double tol = 1e-6L + 1e-14L * mag * den;
+  if (std::abs(c * den - r) < tol) return double(r / den);
+  fprintf(stderr, "coefficient %.17Lg (magnitude %.3Lg) is not a small rational\n", c, mag);
   exit(1);
 }
 
@@ -792,8 +795,8 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
       };
       for (auto &kv : D.acc) {
         cd c = kv.second;
-        if (std::abs(c.imag()) > 1e-9 * (1 + std::abs(c.real()))) { fprintf(stderr, "complex coefficient %g %g\n", c.real(), c.imag()); exit(1); }
-        double cr = snap(c.real());
+        if (std::abs(c.imag()) > 1e-9L * (1 + std::abs(c.real()) + D.mag[kv.first])) { fprintf(stderr, "complex coefficient %Lg %Lg\n", c.real(), c.imag()); exit(1); }
+        double cr = snap(c.real(), D.mag[kv.first]);
         if (cr == 0.0) continue;
         std::string mono, amono;
         std::vector<int> mids;
