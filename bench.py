@@ -41,6 +41,10 @@ ZETA3 = 1.2020569031595942
 TWO_LOOP_TARGET = (197 / 144 + math.pi ** 2 / 12 - math.pi ** 2 * math.log(2) / 2 + 3 * ZETA3 / 4) \
     - (119 / 36 - math.pi ** 2 / 3)
 SIGMA_TARGET = 1e-5
+# samples per graph per step: 6e8 per step on the two-loop set, 1e9 on the
+# three-loop set (BASELINE's config 3 budget)
+DEFAULT_SAMPLES = {1: 1e8, 2: 1e8, 3: 2e7}
+CLOSED_FORM = {1: 0.5, 2: TWO_LOOP_TARGET}
 
 
 def _dist():
@@ -106,19 +110,25 @@ def _peaks():
     return {}
 
 
-def cpu_baseline(n_per_graph=300, seed=0):
-    """The oracle as it stands on this host's cores (numpy, one thread of work)."""
+def cpu_baseline(n_per_graph=None, seed=0, order=2):
+    """The oracle as it stands on this host's cores (numpy, one thread of work),
+    on a bounded sample of the same graph set (about 10-20 s)."""
     from oracle.estimator import weights
     from oracle.graphs import enumerate_graphs
     from oracle.integrand import Integrand
+    graphs = enumerate_graphs(order)
+    if order == 3:
+        graphs = graphs[::10]
+    n_per_graph = n_per_graph or {1: 3000, 2: 300, 3: 20}[order]
     t0 = time.perf_counter()
     tot = 0
-    for sid, g in enumerate(enumerate_graphs(2)):
+    for g in graphs:
+        sid = enumerate_graphs(order).index(g)
         w = weights(Integrand(g), g, sid, seed, 10**12, n_per_graph)
         tot += w.size
     dt = time.perf_counter() - t0
     return {"value": tot / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n_per_graph} samples of each of the 6 two-loop graphs "
+            "sample": f"{n_per_graph} samples of each of {len(graphs)} {order}-loop graphs "
                       f"(Philox counters 1e12.., seed {seed}), {dt:.1f} s"}
 
 
@@ -148,7 +158,7 @@ def run_reference(args):
     from oracle.estimator import weights
     from oracle.graphs import enumerate_graphs
     from oracle.integrand import Integrand
-    graphs = enumerate_graphs(2)
+    graphs = enumerate_graphs(args.order)
     fs = [Integrand(g) for g in graphs]
 
     def step(s):
@@ -168,8 +178,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (Philox counters)",
-        "config": {"workload": "2-loop lepton-loop-free vertex set: 6 graphs, Eq. (1) density, "
-                               "forest-subtracted integrand, FP64", "graphs": 6,
+        "config": {"workload": f"{args.order}-loop lepton-loop-free vertex set: {len(graphs)} graphs, "
+                               "Eq. (1) density, forest-subtracted integrand, FP64 (the CPU oracle)",
+                   "loops": args.order, "graphs": len(graphs),
                    "samples_per_graph_per_step": n, "seed": args.seed},
         "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
                          "sample": f"{n} samples per graph per step, {args.steps} steps"},
@@ -191,8 +202,8 @@ def run_native(args):
     ctx = q.Context(local)
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream)
-    graphs = q.enumerate_graphs(2)
-    S = int(args.samples)
+    graphs = q.enumerate_graphs(args.order)
+    S = int(args.samples if args.samples else DEFAULT_SAMPLES[args.order])
     total = S * len(graphs)
     fp64_peak = q.fp64_peak(local, 50.0)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
@@ -272,15 +283,18 @@ def run_native(args):
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (Philox counters)",
-        "config": {"workload": "2-loop lepton-loop-free vertex set: 6 graphs, 6e8 Philox samples per step "
-                               "shared by running variance, Deg calibrated + gradient-tuned densities, "
-                               "forest-subtracted FP64 integrand, double-double re-evaluation, persistent "
-                               "batched kernel (4 CUDA-graph rounds per step)",
-                   "graphs": 6, "samples_per_step": total, "seed": args.seed, "l2_flush": True,
+        "config": {"workload": f"{args.order}-loop lepton-loop-free vertex set: {len(graphs)} graphs, "
+                               f"{total:.0e} Philox samples per step shared by running variance, Deg "
+                               "calibrated + gradient-tuned densities, forest-subtracted FP64 integrand, "
+                               "double-double re-evaluation, persistent batched kernel (4 CUDA-graph "
+                               "rounds per step)",
+                   "loops": args.order, "graphs": len(graphs), "samples_per_step": total, "seed": args.seed, "l2_flush": True,
                    "launch": {"threads": 256, "items_per_round": n_items, "chunk": chunk},
                    "setup_seconds_calibrate_and_tune": setup_s},
-        "two_loop_total": {"value": tot, "sigma": sigma, "closed_form": TWO_LOOP_TARGET,
-                           "pull": (tot - TWO_LOOP_TARGET) / sigma if sigma > 0 else None,
+        "set_total": {"loops": args.order, "value": tot, "sigma": sigma,
+                           "closed_form": CLOSED_FORM.get(args.order),
+                           "pull": ((tot - CLOSED_FORM[args.order]) / sigma
+                                    if sigma > 0 and args.order in CLOSED_FORM else None),
                            "flagged_fraction": flagged / total_samples,
                            "unstable": sum(r.n_unstable for r in results),
                            "samples_per_graph": [r.n for r in results]},
@@ -297,10 +311,10 @@ def run_native(args):
                 "d2h_bytes_per_step": rounds * n_items * 96},
         "clocks": clk,
     }
-    if ws == 1 and args.compare:
+    if ws == 1 and args.compare and args.order == 2:
         line["plain_per_graph"] = compare_plain(diags, graphs, ctx, S, args.seed, tmax / args.steps, sigma, q)
     if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(order=args.order)
     print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -313,7 +327,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--samples", type=float, default=1e8)
+    ap.add_argument("--samples", type=float, default=None, help="samples per graph per step")
+    ap.add_argument("--order", type=int, default=2, choices=[1, 2, 3], help="loop order of the graph set")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--ref-samples", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
