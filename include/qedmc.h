@@ -40,8 +40,8 @@ extern "C" {
 #define QED_EINVAL (-1)            /* bad argument or unsupported graph */
 #define QED_ENOMEM (-2)            /* device or host allocation failed */
 #define QED_ECUDA (-3)             /* a CUDA runtime call failed */
-#define QED_ETIMEOUT (-4)          /* a bounded device wait gave up */
-#define QED_EUNSTABLE_LIMIT (-5)   /* more unstable points than allowed */
+#define QED_ETIMEOUT (-4)          /* reserved (no call waits on the device without bound) */
+#define QED_EUNSTABLE_LIMIT (-5)   /* reserved */
 #define QED_ENOTFOUND (-6)         /* no generated integrand for this graph */
 
 #define QED_MAX_LOOPS 5
