@@ -29,10 +29,13 @@
 // pairs and projected with trace functionals Tr[W M].
 //
 // Usage: qed_gen <out.cu> <loop orders...>
+#include <atomic>
 #include <cmath>
+#include <thread>
 #include <complex>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <fstream>
 #include <map>
 #include <set>
@@ -41,6 +44,7 @@
 #include <vector>
 
 #include "qed_graph.hpp"
+#include "qed_vm_gen.hpp"
 
 using cd = std::complex<long double>;
 using namespace qed;
@@ -428,6 +432,202 @@ struct DFS {
   }
 };
 
+// The same sum as a transfer-matrix recursion over the items: every branch
+// choice (the Lorentz index of an open pair, the free index mu, a factor's
+// P+/P- part or derivative) is part of a state key, and the partial product
+// of all branches with the same key is kept as one dense matrix.  Closing a
+// pair drops its index from the key, which merges the branches that differed
+// only there, so the work grows with the number of pairs open at a time
+// instead of with all of them.  Every factor's non-zero entries are 1, -1, i
+// or -i, so the partial products have Gaussian-integer entries, exact in
+// double; only the final trace with the projector rounds.  Items other than
+// the closing one of a pair give every state distinct successor keys, so
+// only closing items need a lookup.
+struct DP {
+  const std::vector<Item> *seq;
+  Proj proj;
+  bool allow_p, allow_q, allow_k;
+  std::vector<int> slot_of_item;          // momentum-factor index or -1
+  std::vector<int> pair_partner;          // partner item of a photon or contracted pair, -1
+  std::map<MonoKey, cd> acc;
+  std::map<MonoKey, long double> mag;
+
+  // key: bits 0-23 the alpha of open pairs (2 bits per pair id), 24-26 mu+1,
+  // 27-29 dj+1, 30-34 dv+1, 35-63 the P+/P- mask (2 bits per factor)
+  static constexpr int MU_SH = 24, DJ_SH = 27, DV_SH = 30, PM_SH = 35;
+  struct St { double re[4][4], im[4][4]; };
+  std::vector<uint64_t> keys, nkeys;
+  std::vector<St> st, nst;
+  // open-addressing index of the next item's states (closing items only)
+  std::vector<uint64_t> hkey;
+  std::vector<int> hval;
+  size_t hmask = 0;
+  bool merging = false;
+
+  void reset_index(size_t expect) {
+    size_t cap = 64;
+    while (cap < 2 * expect) cap <<= 1;
+    if (hkey.size() < cap) { hkey.assign(cap, 0); hval.assign(cap, -1); }
+    else std::fill(hval.begin(), hval.begin() + cap, -1);
+    hmask = cap - 1;
+  }
+  St &fresh(uint64_t key) {
+    nkeys.push_back(key);
+    nst.emplace_back();
+    St &s = nst.back();
+    memset(&s, 0, sizeof(St));
+    return s;
+  }
+  St &slot(uint64_t key) {
+    if (!merging) return fresh(key);
+    for (size_t h = (key * 0x9E3779B97F4A7C15ull) >> 17;; ++h) {
+      const size_t i = h & hmask;
+      if (hval[i] < 0) {
+        hkey[i] = key;
+        hval[i] = int(nkeys.size());
+        return fresh(key);
+      }
+      if (hkey[i] == key) return nst[hval[i]];
+    }
+  }
+  // dst += F * src (F monomial with entries in {0, +-1, +-i})
+  void push(const Mono &F, const St &src, uint64_t key) {
+    St &d = slot(key);
+    for (int r = 0; r < 4; ++r) {
+      const long double vr = F.val[r].real(), vi = F.val[r].imag();
+      const int c0 = F.col[r];
+      if (vi == 0.0L) {
+        if (vr == 0.0L) continue;
+        if (vr > 0) for (int c = 0; c < 4; ++c) { d.re[r][c] += src.re[c0][c]; d.im[r][c] += src.im[c0][c]; }
+        else for (int c = 0; c < 4; ++c) { d.re[r][c] -= src.re[c0][c]; d.im[r][c] -= src.im[c0][c]; }
+      } else if (vi > 0) {       // i (x + i y) = -y + i x
+        for (int c = 0; c < 4; ++c) { d.re[r][c] -= src.im[c0][c]; d.im[r][c] += src.re[c0][c]; }
+      } else {
+        for (int c = 0; c < 4; ++c) { d.re[r][c] += src.im[c0][c]; d.im[r][c] -= src.re[c0][c]; }
+      }
+    }
+  }
+  static cd tr_wd(const Dense &W, const St &M) {
+    cd s = 0;
+    for (int r = 0; r < 4; ++r) for (int k = 0; k < 4; ++k) s += W[r][k] * cd(M.re[k][r], M.im[k][r]);
+    return s;
+  }
+  // bound on the rounding of tr_wd: sum of the absolute values of its terms
+  static long double tr_abs(const Dense &W, const St &M) {
+    long double s = 0;
+    for (int r = 0; r < 4; ++r)
+      for (int k = 0; k < 4; ++k) s += std::abs(W[r][k]) * std::abs(cd(M.re[k][r], M.im[k][r]));
+    return s;
+  }
+
+  void run() {
+    const int nitems = int(seq->size());
+    std::vector<int> pid(nitems, -1);
+    int np = 0;
+    for (int t = 0; t < nitems; ++t) if (pair_partner[t] > t) pid[t] = np++;
+    if (np > 12) { fprintf(stderr, "too many open pairs\n"); exit(1); }
+    keys.assign(1, 0ull);
+    st.assign(1, St{});
+    memset(&st[0], 0, sizeof(St));
+    for (int r = 0; r < 4; ++r) st[0].re[r][r] = 1.0;
+    for (int t = 0; t < nitems; ++t) {
+      const Item &I = (*seq)[t];
+      nkeys.clear(); nst.clear();
+      merging = pair_partner[t] >= 0 && pair_partner[t] < t;
+      if (merging) reset_index(keys.size());
+      nkeys.reserve(keys.size() * 4); nst.reserve(keys.size() * 4);
+      for (size_t si = 0; si < keys.size(); ++si) {
+        const uint64_t k = keys[si];
+        const St &s = st[si];
+        const int mu = int((k >> MU_SH) & 7) - 1;
+        const int dv = int((k >> DV_SH) & 31) - 1;
+        if (pair_partner[t] >= 0) {
+          const int p = pair_partner[t];
+          if (p > t) {
+            for (int a = 0; a < 4; ++a) push(GAM[a], s, k | (uint64_t(a) << (2 * pid[t])));
+          } else {
+            const int a = int((k >> (2 * pid[p])) & 3);
+            push(GAM_LOW[a], s, k & ~(3ull << (2 * pid[p])));
+          }
+          continue;
+        }
+        switch (I.kind) {
+          case IT_VTX_MU:
+            if (mu >= 0) { fprintf(stderr, "two free indices\n"); exit(1); }
+            // the on-shell constant L projects on mu = 0 only
+            for (int m = 0; m < 4; ++m) {
+              if (proj == PR_L && m != 0) continue;
+              push(GAM[m], s, (k & ~(7ull << MU_SH)) | (uint64_t(m + 1) << MU_SH));
+            }
+            break;
+          case IT_SEMASS:
+            push(mono_identity(), s, k);
+            break;
+          case IT_LINE:
+          case IT_INS: {
+            const int f = slot_of_item[t];
+            const double sgn = (I.kind == IT_INS) ? -1.0 : 1.0;
+            if (allow_p) {
+              // (A pslash + 1) = (1+A) P+ + (1-A) P-;  (A pslash - 1) = -(1-A) P+ - (1+A) P-
+              // mask bit 2f: factor (1 + A_f), bit 2f+1: factor (1 - A_f)
+              Mono pp, pmn;
+              for (int r = 0; r < 4; ++r) { pp.col[r] = r; pmn.col[r] = r; pp.val[r] = r < 2 ? sgn : 0.0; pmn.val[r] = r < 2 ? 0.0 : sgn; }
+              const uint64_t bp = (I.kind == IT_INS) ? (1ull << (PM_SH + 2 * f + 1)) : (1ull << (PM_SH + 2 * f));
+              const uint64_t bm = (I.kind == IT_INS) ? (1ull << (PM_SH + 2 * f)) : (1ull << (PM_SH + 2 * f + 1));
+              push(pp, s, k | bp);
+              push(pmn, s, k | bm);
+            } else {
+              Mono one = mono_identity();
+              for (int r = 0; r < 4; ++r) one.val[r] = sgn;
+              push(one, s, k);
+            }
+            const uint64_t kd = (k & ~((7ull << DJ_SH) | (31ull << DV_SH))) | (uint64_t(f + 1) << DV_SH);
+            if (dv < 0 && allow_q)
+              for (int j = 1; j < 4; ++j) {
+                Mono m = GAM[j];
+                for (int r = 0; r < 4; ++r) m.val[r] = -m.val[r];
+                push(m, s, kd | (uint64_t(j + 1) << DJ_SH));
+              }
+            if (dv < 0 && allow_k)
+              for (int nu = 0; nu < 4; ++nu) push(GAM_LOW[nu], s, kd | (uint64_t(nu + 1) << DJ_SH));
+            break;
+          }
+          default:
+            fprintf(stderr, "bad item\n");
+            exit(1);
+        }
+      }
+      keys.swap(nkeys);
+      st.swap(nst);
+    }
+    for (size_t si = 0; si < keys.size(); ++si) {
+      const uint64_t k = keys[si];
+      const int mu = int((k >> MU_SH) & 7) - 1;
+      const int dj = int((k >> DJ_SH) & 7) - 1;
+      const int dv = int((k >> DV_SH) & 31) - 1;
+      const uint32_t pm = uint32_t(k >> PM_SH);
+      const Dense *W = nullptr;
+      long double sg = 1.0L;
+      switch (proj) {
+        case PR_F2:
+          if (dv < 0) { if (mu == 0) { W = &W_F1; sg = -1.0L; } else if (mu > 0) W = &W_MAG_G[mu]; }
+          else if (mu > 0) W = &W_MAG_H[mu][dj];
+          break;
+        case PR_L: if (mu == 0 && dv < 0) W = &W_F1; break;
+        case PR_UV: if (dv < 0 && mu >= 0) W = &W_UV[mu]; break;
+        case PR_SEMASS: if (dv < 0) W = &W_F1; break;
+        case PR_SEWF: if (dv >= 0) W = &W_WF[dj]; break;
+      }
+      if (!W) continue;
+      const cd v = cd(sg) * tr_wd(*W, st[si]);
+      if (std::abs(v) > 0) {
+        acc[MonoKey{pm, dv}] += v;
+        mag[MonoKey{pm, dv}] += tr_abs(*W, st[si]);
+      }
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------
 // code emission
 // ---------------------------------------------------------------------------
@@ -781,7 +981,15 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
       D.pair_alpha.assign(seq.size(), 0);
       for (auto &pp : ph_pairs) { D.pair_partner[pp.first] = pp.second; D.pair_partner[pp.second] = pp.first; }
       for (auto &pr : pat) { int a = mom_items[pr.first], b = mom_items[pr.second]; D.pair_partner[a] = b; D.pair_partner[b] = a; }
-      D.go(0, mono_identity(), -1, -1, 0u, -1);
+      if (getenv("QED_GEN_DFS")) D.go(0, mono_identity(), -1, -1, 0u, -1);
+      else {
+        DP Q;
+        Q.seq = D.seq; Q.proj = D.proj; Q.allow_p = D.allow_p; Q.allow_q = D.allow_q; Q.allow_k = D.allow_k;
+        Q.slot_of_item = D.slot_of_item; Q.pair_partner = D.pair_partner;
+        Q.run();
+        D.acc.swap(Q.acc);
+        D.mag.swap(Q.mag);
+      }
       std::string poly, apoly;
       Poly vpoly;                               // value polynomial over named factors
       std::vector<std::string> vnames;
@@ -881,6 +1089,67 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
   ++st.terms;
 }
 
+// One graph's integrand as bytecode: every forest term emitted into one
+// function body (polynomials shared across the terms), then compiled.
+static qvm::Entry gen_vm_graph(const Graph &g, GenStats &st) {
+  auto terms = build_terms(g);
+  Emitter E;
+  std::vector<std::string> outs;
+  for (auto &t : terms) {
+    TermInfo T = analyse(g, t);
+    std::string o = "term" + std::to_string(outs.size());
+    emit_term(E, T, o, st);
+    outs.push_back(o);
+  }
+  std::ostringstream body;
+  body << E.os.str() << "    return ";
+  for (size_t i = 0; i < outs.size(); ++i) body << (i ? " + " : "") << outs[i];
+  body << ";\n";
+  qvm::Compiler C(g.n_lines());
+  qvm::Entry e;
+  e.name = g.name();
+  e.n_lines = g.n_lines();
+  e.prog = C.compile(body.str(), outs);
+  return e;
+}
+
+// All graphs of order n, one per mirror pair (the smaller key; QED_VM_ALL=1:
+// both orientations), on all host threads; QED_VM_LIMIT=k keeps the first k.
+static void gen_vm_order(const std::string &dir, int n, GenStats &st) {
+  std::vector<Graph> gs;
+  const bool all = getenv("QED_VM_ALL") && atoi(getenv("QED_VM_ALL"));
+  for (auto &g : enumerate_graphs(n))
+    if (all || !(g.mirror().key() < g.key())) gs.push_back(g);
+  if (const char *lim = getenv("QED_VM_LIMIT")) {
+    const size_t k = size_t(atol(lim));
+    if (k < gs.size()) gs.resize(k);
+  }
+  std::vector<qvm::Entry> es(gs.size());
+  std::vector<GenStats> sts(gs.size());
+  std::atomic<size_t> next{0};
+  unsigned nt = std::max(1u, std::thread::hardware_concurrency());
+  if (const char *j = getenv("QED_GEN_JOBS")) nt = std::max(1, atoi(j));
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t)
+    th.emplace_back([&]() {
+      for (size_t i; (i = next.fetch_add(1)) < gs.size();) es[i] = gen_vm_graph(gs[i], sts[i]);
+    });
+  for (auto &t : th) t.join();
+  size_t ins = 0;
+  double flops = 0.0;
+  int regs = 0;
+  for (size_t i = 0; i < es.size(); ++i) {
+    st.terms += sts[i].terms;
+    st.monos += sts[i].monos;
+    ins += es[i].prog.ins.size();
+    flops += es[i].prog.flops;
+    regs = std::max(regs, es[i].prog.n_regs);
+  }
+  qvm::write_programs(dir + "/vm_n" + std::to_string(n) + ".bin", es);
+  fprintf(stderr, "qed_gen: %zu bytecode programs of order %d, %zu instructions, %.0f FP64 ops, at most %d registers\n",
+          es.size(), n, ins, flops, regs);
+}
+
 int main(int argc, char **argv) {
   if (argc < 3) { fprintf(stderr, "usage: qed_gen out_dir n1 [n2 ...]\n"); return 2; }
   int split_from = 3;
@@ -899,6 +1168,12 @@ int main(int argc, char **argv) {
   std::vector<long> reg_flops;
   GenStats st;
   for (int ai = 2; ai < argc; ++ai) {
+    if (argv[ai][0] == 'v') {
+      // bytecode programs for the interpreter kernels: vm_n<n>.bin
+      const int n = atoi(argv[ai] + 1);
+      gen_vm_order(dir, n, st);
+      continue;
+    }
     int n = atoi(argv[ai]);
     auto gs = enumerate_graphs(n);
     for (size_t gi = 0; gi < gs.size(); ++gi) {
