@@ -20,9 +20,25 @@ from __future__ import annotations
 import numpy as np
 
 
+def _det_laplace(m):
+    """Determinant of [B, k, k] by Laplace expansion along the first row."""
+    k = m.shape[1]
+    if k == 1:
+        return m[:, 0, 0]
+    if k == 2:
+        return m[:, 0, 0] * m[:, 1, 1] - m[:, 0, 1] * m[:, 1, 0]
+    tot = None
+    for c in range(k):
+        minor = np.delete(np.delete(m, 0, axis=1), c, axis=2)
+        term = m[:, 0, c] * _det_laplace(minor)
+        tot = term if tot is None else (tot + term if c % 2 == 0 else tot - term)
+    return tot
+
+
 def _det_adj_cofactor(lam):
-    """Determinant and adjugate by cofactor expansion (any float dtype,
-    n <= 3); used for the extended-precision mode."""
+    """Determinant and adjugate by cofactor expansion (any float dtype);
+    used for the extended-precision mode.  adj[r, c] = (-1)^(r+c) times the
+    minor of lam without row c and column r."""
     B, n, _ = lam.shape
     if n == 1:
         return lam[:, 0, 0].copy(), np.ones_like(lam)
@@ -43,7 +59,15 @@ def _det_adj_cofactor(lam):
                 adj[:, r, c] = (-1) ** (r + c) * (m[:, 0, 0] * m[:, 1, 1] - m[:, 0, 1] * m[:, 1, 0])
         det = lam[:, 0, 0] * adj[:, 0, 0] + lam[:, 0, 1] * adj[:, 1, 0] + lam[:, 0, 2] * adj[:, 2, 0]
         return det, adj
-    raise ValueError("extended precision supports n <= 3")
+    adj = np.empty_like(lam)
+    for r in range(n):
+        for c in range(n):
+            minor = np.delete(np.delete(lam, c, axis=1), r, axis=2)
+            adj[:, r, c] = (-1) ** (r + c) * _det_laplace(minor)
+    det = lam[:, 0, 0] * adj[:, 0, 0]
+    for c in range(1, n):
+        det = det + lam[:, 0, c] * adj[:, c, 0]
+    return det, adj
 
 
 def polynomials(z, eta, alpha, beta, kappa, mass2, dtype=np.float64):

@@ -25,6 +25,21 @@ def test_u_is_kirchhoff_spanning_tree_sum(n):
         assert P["U"][0] == pytest.approx(spanning_tree_u(edges, 2 * g.n + 1, z), rel=1e-12)
 
 
+@pytest.mark.parametrize("n", [4, 5])
+def test_extended_precision_u_and_adjugate(n):
+    """The long-double path (cofactor expansion) at four and five loops:
+    U against the spanning-tree sum, adj against det * inverse."""
+    rng = np.random.default_rng(10 + n)
+    for g in enumerate_graphs(n)[:: 97 if n == 4 else 1201][:4]:
+        ev = _main_term(g)
+        z = rng.random(g.n_lines) + 0.1
+        P = polynomials(z, ev.eta, ev.alpha, ev.beta, ev.kappa, ev.mass2, dtype=np.longdouble)
+        P64 = polynomials(z, ev.eta, ev.alpha, ev.beta, ev.kappa, ev.mass2)
+        edges = [g.line_ends(l) for l in range(g.n_lines)]
+        assert float(P["U"][0]) == pytest.approx(spanning_tree_u(edges, 2 * g.n + 1, z), rel=1e-13)
+        np.testing.assert_allclose(P["adj"][0].astype(float), P64["adj"][0], rtol=1e-10, atol=1e-14)
+
+
 def test_b_diagonal_is_derivative_of_u():
     g = enumerate_graphs(2)[1]
     ev = _main_term(g)
