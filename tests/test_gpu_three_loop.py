@@ -52,7 +52,11 @@ def test_three_loop_points_match_oracle(ctx, gi, begin, count):
     fld = Integrand(og)(z, dtype=np.longdouble).astype(np.float64)
     fo = Integrand(og)(z)
     ok = fl == 0
-    tol = 1e-12 * np.abs(fld) + 8.0 * 2.0 ** -11 * np.abs(fo - fld)
+    # the long-double oracle's own error: its 11 extra bits do not cut the
+    # realised error by 2^11 at strongly cancelling points (measured against
+    # mpmath at 40 digits: 1/51 of the FP64 error at a point with
+    # kappa ~ 4e11), so it is bounded here by |f64 - ld| / 16
+    tol = 1e-12 * np.abs(fld) + np.abs(fo - fld) / 16.0
     bad = (np.abs(f - fld) > tol) & ok
     assert bad.sum() <= max(1, count // 16), np.abs(f - fld)[bad] / np.abs(fld[bad])
     fdd = d.eval_points(torch.tensor(z, device="cuda"), prec=1).cpu().numpy()
