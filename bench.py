@@ -43,7 +43,9 @@ TWO_LOOP_TARGET = (197 / 144 + math.pi ** 2 / 12 - math.pi ** 2 * math.log(2) / 
 SIGMA_TARGET = 1e-5
 # samples per graph per step: 6e8 per step on the two-loop set, 1e9 on the
 # three-loop set (BASELINE's config 3 budget)
-DEFAULT_SAMPLES = {1: 1e8, 2: 1e8, 3: 2e7}
+DEFAULT_SAMPLES = {1: 1e8, 2: 1e8, 3: 2e7, 4: 2 ** 17}
+# work-item size of the batched kernel per order (a four-loop sample is ~1e5 FP64 operations)
+CHUNK = {1: 1 << 18, 2: 1 << 18, 3: 1 << 18, 4: 1 << 13}
 CLOSED_FORM = {1: 0.5, 2: TWO_LOOP_TARGET}
 
 
@@ -110,6 +112,27 @@ def _peaks():
     return {}
 
 
+def mirror_weights(graphs):
+    """2 - [self-mirror] per graph of a mirror-reduced set (Sec. 3 counts each
+    mirror pair once; the set total is the weighted sum)."""
+    w = []
+    for g in graphs:
+        m = 2 * g.n - 1
+        mp = tuple(sorted((min(m - s, m - t), max(m - s, m - t)) for s, t in g.pairs))
+        w.append(1.0 if (mp, 2 * g.n - g.e) == (tuple(g.pairs), g.e) else 2.0)
+    return w
+
+
+def graph_set(q, order):
+    """The benchmarked set: every graph up to three loops (mirror pairs both
+    present), one per mirror pair from four loops on (bytecode integrands)."""
+    if order >= 4:
+        gs = q.enumerate_graphs(order, reduced=True)
+        return gs, mirror_weights(gs)
+    gs = q.enumerate_graphs(order)
+    return gs, [1.0] * len(gs)
+
+
 def cpu_baseline(n_per_graph=None, seed=0, order=2):
     """The oracle as it stands on this host's cores (numpy, one thread of work),
     on a bounded sample of the same graph set (about 10-20 s)."""
@@ -119,7 +142,9 @@ def cpu_baseline(n_per_graph=None, seed=0, order=2):
     graphs = enumerate_graphs(order)
     if order == 3:
         graphs = graphs[::10]
-    n_per_graph = n_per_graph or {1: 3000, 2: 300, 3: 20}[order]
+    if order == 4:
+        graphs = graphs[85:86]
+    n_per_graph = n_per_graph or {1: 3000, 2: 300, 3: 20, 4: 2}[order]
     t0 = time.perf_counter()
     tot = 0
     for g in graphs:
@@ -139,11 +164,12 @@ def compare_plain(diags, graphs, ctx, S, seed, t_step, sigma_step, q):
     plain = [ctx.load(g) for g in graphs]
     res = [d.integrate(S, seed=seed + 1, begin=1 << 41) for d in plain]
     t = sum(r.seconds for r in res)
-    sig = math.sqrt(sum(r.variance for r in res))
+    mw = mirror_weights(graphs) if graphs[0].n >= 4 else [1.0] * len(graphs)
+    sig = math.sqrt(sum(w * w * r.variance for w, r in zip(mw, res)))
     tts_plain = t * (sig / SIGMA_TARGET) ** 2
     tts_batch = t_step * (sigma_step / SIGMA_TARGET) ** 2
     return {"seconds": t, "samples_per_s": S * len(graphs) / t, "sigma": sig,
-            "total": sum(r.value for r in res), "time_to_sigma": tts_plain,
+            "total": sum(w * r.value for w, r in zip(mw, res)), "time_to_sigma": tts_plain,
             "kernel_seconds": sum(r.kernel_seconds for r in res),
             "speedup_time_to_sigma_batched_tuned_vs_plain": tts_plain / tts_batch,
             "note": "the plain densities give heavy-tailed weights on the self-energy graphs, so "
@@ -159,6 +185,10 @@ def run_reference(args):
     from oracle.graphs import enumerate_graphs
     from oracle.integrand import Integrand
     graphs = enumerate_graphs(args.order)
+    if args.order >= 4:
+        # bounded sample: a four-loop point costs the oracle seconds
+        graphs = graphs[85::108]
+        n = 1
     fs = [Integrand(g) for g in graphs]
 
     def step(s):
@@ -202,7 +232,7 @@ def run_native(args):
     ctx = q.Context(local)
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream)
-    graphs = q.enumerate_graphs(args.order)
+    graphs, mw = graph_set(q, args.order)
     S = int(args.samples if args.samples else DEFAULT_SAMPLES[args.order])
     total = S * len(graphs)
     fp64_peak = q.fp64_peak(local, 50.0)
@@ -210,12 +240,13 @@ def run_native(args):
     # set-up (not timed): Deg calibrated on the integrand, densities tuned
     t0 = time.perf_counter()
     diags = [ctx.load(g) for g in graphs]
+    nb, ts, tn = (8, 10, 1 << 21) if args.order <= 3 else (2, 4, 1 << 15)
     for d in diags:
-        d.calibrate_deg(n_base=8, seed=args.seed + 5)
-        tune(d, steps=10, n=1 << 21, lr=0.08, seed=args.seed + 7)
+        d.calibrate_deg(n_base=nb, seed=args.seed + 5)
+        tune(d, steps=ts, n=tn, lr=0.08, seed=args.seed + 7)
     setup_s = time.perf_counter() - t0
     flops = [d.flops_per_sample() for d in diags]
-    rounds, chunk = 4, 1 << 18
+    rounds, chunk = 4, CHUNK[args.order]
 
     def step(s):
         base = (s * ws + rank) * total + (1 << 40)      # fresh counters every step and rank
@@ -273,8 +304,8 @@ def run_native(args):
         return 0
     total_samples = ws * nsamp
     value = total_samples / tmax
-    tot = sum(r.value for r in results)
-    sigma = math.sqrt(sum(r.variance for r in results))
+    tot = sum(w * r.value for w, r in zip(mw, results))
+    sigma = math.sqrt(sum(w * w * r.variance for w, r in zip(mw, results)))
     achieved = alg / ksec / 1e12
     peak = fp64_peak / 1e12
     n_items = max(len(diags), (total // rounds + chunk - 1) // chunk)
@@ -283,7 +314,8 @@ def run_native(args):
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (Philox counters)",
-        "config": {"workload": f"{args.order}-loop lepton-loop-free vertex set: {len(graphs)} graphs, "
+        "config": {"workload": f"{args.order}-loop lepton-loop-free vertex set: {len(graphs)} graphs"
+                               + (" (one per mirror pair, bytecode integrands)" if args.order >= 4 else "") + ", "
                                f"{total:.0e} Philox samples per step shared by running variance, Deg "
                                "calibrated + gradient-tuned densities, forest-subtracted FP64 integrand, "
                                "double-double re-evaluation, persistent batched kernel (4 CUDA-graph "
@@ -302,7 +334,8 @@ def run_native(args):
                           "sigma_reached": sigma, "seconds_run": tmax},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_batch_fp64 (persistent FP64 integration kernel)",
+                     "kernel": ("k_batch_fp64 (persistent FP64 integration kernel)" if args.order <= 3 else
+                                "k_batch_vm_fp64<12> (persistent FP64 interpreter kernel, bytecode integrands)"),
                      "peak_source": "measured FP64 FMA throughput (qed_fp64_peak), of measured",
                      "flops_per_sample": {str(i): f for i, f in enumerate(flops)}},
         "gpu_launches": launches,
@@ -311,7 +344,7 @@ def run_native(args):
                 "d2h_bytes_per_step": rounds * n_items * 96},
         "clocks": clk,
     }
-    if ws == 1 and args.compare and args.order == 2:
+    if ws == 1 and args.compare and args.order in (2, 4):
         line["plain_per_graph"] = compare_plain(diags, graphs, ctx, S, args.seed, tmax / args.steps, sigma, q)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(order=args.order)
@@ -328,7 +361,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--samples", type=float, default=None, help="samples per graph per step")
-    ap.add_argument("--order", type=int, default=2, choices=[1, 2, 3], help="loop order of the graph set")
+    ap.add_argument("--order", type=int, default=2, choices=[1, 2, 3, 4], help="loop order of the graph set")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--ref-samples", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -86,8 +86,13 @@ typedef struct {
 } qed_result;
 
 /* ---- context ------------------------------------------------------------ */
-/* Create a context on CUDA device `device`.  flags: reserved, pass 0.  The
- * context owns every device buffer it allocates. */
+/* Context flag: graphs loaded on this context use a registered bytecode
+ * program (qed_programs_load) even where a compiled integrand exists (used to
+ * compare the two paths on the same graph). */
+#define QED_CTX_PREFER_PROGRAMS 1u
+/* Create a context on CUDA device `device`.  flags: 0 or
+ * QED_CTX_PREFER_PROGRAMS (other bits: QED_EINVAL).  The context owns every
+ * device buffer it allocates. */
 int qed_ctx_create(int device, uint64_t flags, qed_ctx **out);
 int qed_ctx_destroy(qed_ctx *ctx);
 /* Launch subsequent work on this cudaStream_t (0 = legacy default stream). */
@@ -115,13 +120,29 @@ int qed_enumerate(int n, int reduced, qed_graph *out, int cap, int *count);
  * the larger and on the smaller side of X. */
 int qed_gauge_class(const qed_graph *g, int kmn[3]);
 
+/* Register bytecode integrands with the context.  Sec. 2 makes every graph's
+ * contribution one parametric integral of a generated, forest-subtracted
+ * integrand; Sec. 3 notes that the generated code for the 5-loop set reaches
+ * 500 GB.  From four loops on, the generator therefore writes each
+ * integrand as a program for the library's interpreter kernels instead of
+ * source to compile.  data/bytes: the contents of a program file written by
+ * the generator (vm_n<n>.bin: "QEDVM001", count, then per program its graph
+ * name, line count, register count, instruction words and constants), in
+ * host memory, owned by the caller and copied to the device.  Every
+ * instruction is checked against its program's register and constant counts
+ * (QED_EINVAL on any violation, nothing registered); *count (may be NULL)
+ * receives the number of programs added. */
+int qed_programs_load(qed_ctx *ctx, const void *data, size_t bytes, int *count);
+
 /* Load a graph: validate it (lepton-loop free, one-particle irreducible, no
- * self-energy on an external leg), select its generated integrand, build and
- * upload the Eq. (1) tables.  QED_ENOTFOUND if the library holds no generated
- * integrand for this graph. */
+ * self-energy on an external leg), select its integrand -- the compiled one,
+ * else a registered bytecode program of the same graph (always the program
+ * on a QED_CTX_PREFER_PROGRAMS context) -- and build and upload the Eq. (1)
+ * tables.  QED_ENOTFOUND if neither exists for this graph. */
 int qed_diagram_load(qed_ctx *ctx, const qed_graph *g, const qed_pdf *pdf, qed_diag **out);
 int qed_diagram_free(qed_diag *d);
-/* N = 3n lines, generated integrand id, log of the Eq. (1) normaliser F(E). */
+/* N = 3n lines, integrand id (compiled: 0..count-1; bytecode program:
+ * count + its registration index), log of the Eq. (1) normaliser F(E). */
 int qed_diagram_info(const qed_diag *d, int *n_lines, int *integrand_id, double *log_norm);
 
 /* ---- integration (Sec. 2 nonadaptive MC, Sec. 3) ------------------------- */
@@ -177,7 +198,9 @@ typedef struct {
   uint64_t counter_base; /* first Philox counter of every graph's samples (default 0) */
 } qed_batch_opts;
 
-/* Integrate the k graphs d[0..k-1] (all loaded on the same context) with
+/* Integrate the k graphs d[0..k-1] (all loaded on the same context; all
+ * with compiled integrands, or all with bytecode programs of one loop order,
+ * else QED_EINVAL) with
  * total_samples samples in all, in one persistent launch per round: blocks
  * take (graph, counter-block) work items from a device queue, so graphs of
  * different cost share the GPU.  After round r the samples of round r+1 are
@@ -218,7 +241,8 @@ int qed_fp64_peak(int device, double ms, double *flops_per_s);
  * found again by re-scanning the chunk instead of being queued.  All calls in
  * the process share the array, so calls that overlap on the GPU (other
  * threads, other streams) race: serialise them.  Each call clears the
- * counters it needs before use. */
+ * counters it needs before use.  Compiled integrands only: a graph that
+ * uses a bytecode program gives QED_EINVAL. */
 int qed_integrate_range_noalloc(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed, qed_result *out);
 
 #ifdef __cplusplus

@@ -146,6 +146,7 @@ def load_library():
         "qed_fp64_peak": (C.c_int, [C.c_int, C.c_double, P(C.c_double)]),
         "qed_diagram_calibrate_deg": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64]),
         "qed_diagram_get_deg": (C.c_int, [C.c_void_p, P(C.c_double)]),
+        "qed_programs_load": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, P(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -191,21 +192,46 @@ def merge_results(a: Result, b: Result) -> Result:
     return Result._from_c(co)
 
 
+QED_CTX_PREFER_PROGRAMS = 1
+
+
+def program_files():
+    """Bytecode integrand files written by the build (vm_n<n>.bin)."""
+    return sorted((_HERE / "csrc" / "_gen").glob("vm_n*.bin"))
+
+
 class Context:
-    """qed_ctx: one CUDA device; owns the device buffers it allocates."""
+    """qed_ctx: one CUDA device; owns the device buffers it allocates.
+
+    The bytecode integrands the build wrote (four loops and up, and the
+    lower orders for comparison) are registered on creation unless
+    programs=False; prefer_programs=True makes graphs that also have a
+    compiled integrand use their program (QED_CTX_PREFER_PROGRAMS)."""
 
     def __init__(self, device: int = 0, threads: int | None = None, blocks: int | None = None,
-                 threshold: float | None = None, stream=None):
+                 threshold: float | None = None, stream=None, programs: bool = True,
+                 prefer_programs: bool = False):
         L = load_library()
         self._h = C.c_void_p()
-        _check(L.qed_ctx_create(device, 0, C.byref(self._h)))
+        _check(L.qed_ctx_create(device, QED_CTX_PREFER_PROGRAMS if prefer_programs else 0, C.byref(self._h)))
         self.device = device
+        self.n_programs = 0
+        if programs:
+            for f in program_files():
+                self.programs_load(f.read_bytes())
         if threads is not None or blocks is not None:
             self.set_launch(threads or 256, blocks or 0)
         if threshold is not None:
             _check(L.qed_ctx_set_threshold(self._h, threshold))
         if stream is not None:
             self.set_stream(stream)
+
+    def programs_load(self, data: bytes) -> int:
+        """qed_programs_load: register the bytecode integrands of a program file."""
+        cnt = C.c_int(0)
+        _check(load_library().qed_programs_load(self._h, data, len(data), C.byref(cnt)))
+        self.n_programs += cnt.value
+        return cnt.value
 
     def set_launch(self, threads: int, blocks: int = 0):
         _check(load_library().qed_ctx_set_launch(self._h, threads, blocks))

@@ -1,14 +1,19 @@
 """Build the native library in-tree: run the integrand generator, then nvcc.
 
-    python -m paper_1905_08007_b300.build [--orders 1 2 3] [--jobs 8]
+    python -m paper_1905_08007_b300.build [--orders 1 2 3] [--programs 2 3 4] [--jobs 8]
 
 Steps:
 1. compile ``csrc/qed_gen.cpp`` with g++ and run it for the requested loop
    orders; it writes ``csrc/_gen/g_<id>.cuh`` (one device function per vertex
    graph, the forest-subtracted integrand) and ``csrc/_gen/qed_registry.h``;
 2. compile one translation unit per graph (the kernels instantiated for that
-   integrand) plus ``csrc/qedmc.cu`` (host side, C ABI) for sm_103a, in
-   parallel, and link them into ``libqedmc.so`` next to this file.
+   integrand) plus ``csrc/qedmc.cu`` (host side, C ABI, the interpreter
+   kernels) for sm_103a, in parallel, and link them into ``libqedmc.so`` next
+   to this file;
+3. run the generator's bytecode back end for the program orders: it writes
+   ``csrc/_gen/vm_n<n>.bin`` (one program per mirror-reduced graph), which the
+   library's interpreter kernels evaluate (four loops and up have no compiled
+   integrands; the lower orders are there to compare the two paths).
 """
 from __future__ import annotations
 
@@ -30,6 +35,7 @@ INCLUDE = ROOT / "include"
 BUILD = ROOT / "_build"
 LIB = PKG / "libqedmc.so"
 DEFAULT_ORDERS = (1, 2, 3)
+DEFAULT_PROGRAM_ORDERS = (2, 3, 4)
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -52,28 +58,63 @@ def _digest(paths, extra=""):
     return h.hexdigest()
 
 
-def build(orders=DEFAULT_ORDERS, force=False, verbose_ptxas=False, jobs=None):
+GEN_SRC = [CSRC / "qed_gen.cpp", CSRC / "qed_graph.hpp", CSRC / "qed_vm_gen.hpp"]
+
+
+def _generator():
+    gen_bin = BUILD / "qed_gen"
+    key = _digest(GEN_SRC)
+    stamp = BUILD / "qed_gen.stamp"
+    if not (gen_bin.exists() and stamp.exists() and stamp.read_text() == key):
+        _run(["g++", "-O3", "-std=c++17", "-pthread", "-o", gen_bin, CSRC / "qed_gen.cpp"])
+        stamp.write_text(key)
+    return gen_bin
+
+
+def build_programs(orders=DEFAULT_PROGRAM_ORDERS, force=False):
+    """Bytecode programs vm_n<n>.bin for the interpreter kernels."""
     orders = tuple(int(o) for o in orders)
     BUILD.mkdir(exist_ok=True)
     GEN.mkdir(exist_ok=True)
-    gen_src = [CSRC / "qed_gen.cpp", CSRC / "qed_graph.hpp"]
+    outs = [GEN / f"vm_n{n}.bin" for n in orders]
+    stamp = BUILD / "programs.stamp"
+    key = _digest(GEN_SRC, extra=repr(orders))
+    if not force and all(o.exists() for o in outs) and stamp.exists() and stamp.read_text() == key:
+        return outs
+    for old in GEN.glob("vm_n*.bin"):
+        old.unlink()
+    if orders:
+        _run([_generator(), GEN] + [f"v{n}" for n in orders])
+    stamp.write_text(key)
+    return outs
+
+
+def build(orders=DEFAULT_ORDERS, force=False, verbose_ptxas=False, jobs=None,
+          program_orders=DEFAULT_PROGRAM_ORDERS):
+    lib = build_library(orders, force, verbose_ptxas, jobs)
+    build_programs(program_orders, force)
+    return lib
+
+
+def build_library(orders=DEFAULT_ORDERS, force=False, verbose_ptxas=False, jobs=None):
+    orders = tuple(int(o) for o in orders)
+    BUILD.mkdir(exist_ok=True)
+    GEN.mkdir(exist_ok=True)
     lib_src = [CSRC / "qedmc.cu", CSRC / "qed_kernels.cuh", CSRC / "qed_batch.cuh", CSRC / "qed_dd.cuh",
-               CSRC / "qed_graph.hpp", INCLUDE / "qedmc.h"]
+               CSRC / "qed_vm.cuh", CSRC / "qed_graph.hpp", INCLUDE / "qedmc.h"]
     stamp = BUILD / "libqedmc.stamp"
-    key = _digest(gen_src + lib_src, extra=repr(orders) + ARCH + repr(verbose_ptxas))
+    key = _digest(GEN_SRC + lib_src, extra=repr(orders) + ARCH + repr(verbose_ptxas))
     if not force and LIB.exists() and stamp.exists() and stamp.read_text() == key:
         return LIB
-    gen_bin = BUILD / "qed_gen"
-    _run(["g++", "-O2", "-std=c++17", "-o", gen_bin, CSRC / "qed_gen.cpp"])
-    for old in GEN.glob("*"):
-        old.unlink()
+    gen_bin = _generator()
+    for pat in ("g_*.cuh", "k_*.cu", "qed_registry.h"):
+        for old in GEN.glob(pat):
+            old.unlink()
     _run([gen_bin, GEN] + list(orders))
     reg = (GEN / "qed_registry.h").read_text()
     ids = re.findall(r"X\((\d+), (\d+)\)", reg.split("QED_GENERATED_LIST(X)")[1].splitlines()[0])
     objdir = BUILD / "obj"
     objdir.mkdir(exist_ok=True)
-    for old in objdir.glob("*.o"):
-        old.unlink()
     big = [(gid, ln) for gid, ln in ids if int(ln) >= 9]      # three loops and up
     rdc = bool(big)
     base = [_nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -84,6 +125,7 @@ def build(orders=DEFAULT_ORDERS, force=False, verbose_ptxas=False, jobs=None):
         base.append("-Xptxas=-v")
     units = []
     bigset = {gid for gid, _ in big}
+    kern_h = [CSRC / "qed_kernels.cuh", CSRC / "qed_dd.cuh"]
     for gid, lines in ids:
         tu = GEN / f"k_{gid}.cu"
         text = f'#include "qed_kernels.cuh"\n#include "g_{gid}.cuh"\nQED_DEFINE_KSET({gid}, {lines})\n'
@@ -94,7 +136,7 @@ def build(orders=DEFAULT_ORDERS, force=False, verbose_ptxas=False, jobs=None):
                      f"__device__ dd qed_ext_dd_{gid}(const dd* z, double& a) "
                      f"{{ return qed_gen_f<{gid}>::template eval<dd>(z, a); }}\n")
         tu.write_text(text)
-        units.append((tu, objdir / f"k_{gid}.o"))
+        units.append((tu, objdir / f"k_{gid}.o", kern_h + [GEN / f"g_{gid}.cuh"]))
     # the persistent batched kernels: one switch over every generated graph;
     # graphs of three loops and up are linked in (relocatable device code)
     # rather than compiled again here
@@ -120,15 +162,24 @@ def build(orders=DEFAULT_ORDERS, force=False, verbose_ptxas=False, jobs=None):
         f'  switch (B.diags[I.diag].fid) {{ {c64} default: break; }}\n}}\n'
         f'__device__ void batch_dispatch_dd(const BatchParams &B, unsigned int it, const BatchItem &I, double *smem) {{\n'
         f'  switch (B.diags[I.diag].fid) {{ {cdd} default: break; }}\n}}\n')
-    units.append((btu, objdir / "k_batch.o"))
-    units.append((CSRC / "qedmc.cu", objdir / "qedmc.o"))
+    units.append((btu, objdir / "k_batch.o",
+                  kern_h + [CSRC / "qed_batch.cuh"] + [GEN / f"g_{gid}.cuh" for gid, _ in ids if gid not in bigset]))
+    units.append((CSRC / "qedmc.cu", objdir / "qedmc.o",
+                  sorted(CSRC.glob("*.cuh")) + [CSRC / "qed_graph.hpp", INCLUDE / "qedmc.h", GEN / "qed_registry.h"]))
 
     def compile_one(u):
-        src, obj = u
+        # an object is reused when its source, the headers it includes and
+        # the flags are unchanged
+        src, obj, deps = u
         cmd = base + ["-c", "-o", obj, src]
+        okey = _digest([src] + list(deps), extra=" ".join(str(c) for c in cmd))
+        ostamp = obj.with_suffix(".stamp")
+        if obj.exists() and ostamp.exists() and ostamp.read_text() == okey:
+            return src, ""
         r = subprocess.run([str(c) for c in cmd], capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
+        ostamp.write_text(okey)
         return src, r.stderr
 
     jobs = jobs or max(1, os.cpu_count() or 1)
@@ -137,8 +188,12 @@ def build(orders=DEFAULT_ORDERS, force=False, verbose_ptxas=False, jobs=None):
         for src, err in ex.map(compile_one, units):
             if verbose_ptxas and err:
                 print(f"== {src.name}\n{err}")
+    keep = {o for _, o, _ in units}
+    for old in objdir.glob("*.o"):
+        if old not in keep:
+            old.unlink()
     _run([_nvcc(), ARCH, "-shared"] + (["-rdc=true"] if rdc else []) + ["-o", LIB] +
-         [o for _, o in units] + ["-lcudart"])
+         [o for _, o, _ in units] + ["-lcudart"])
     stamp.write_text(key)
     return LIB
 
@@ -146,11 +201,12 @@ def build(orders=DEFAULT_ORDERS, force=False, verbose_ptxas=False, jobs=None):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--orders", nargs="*", type=int, default=list(DEFAULT_ORDERS))
+    ap.add_argument("--programs", nargs="*", type=int, default=list(DEFAULT_PROGRAM_ORDERS))
     ap.add_argument("--force", action="store_true")
     ap.add_argument("--ptxas-v", action="store_true")
     ap.add_argument("--jobs", type=int, default=None)
     a = ap.parse_args(argv)
-    print(build(a.orders, force=a.force, verbose_ptxas=a.ptxas_v, jobs=a.jobs))
+    print(build(a.orders, force=a.force, verbose_ptxas=a.ptxas_v, jobs=a.jobs, program_orders=a.programs))
 
 
 if __name__ == "__main__":

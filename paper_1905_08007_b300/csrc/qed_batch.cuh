@@ -21,6 +21,10 @@ struct BatchDiag {
   int fid;
   int N;
   int pad;
+  // bytecode integrand (fid < 0): program, constants, their counts
+  const uint32_t *vins;
+  const double *vkon;
+  int vnk, vnr;
 };
 
 struct BatchItem {

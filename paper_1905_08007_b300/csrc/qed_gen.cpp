@@ -471,28 +471,39 @@ struct DP {
     else std::fill(hval.begin(), hval.begin() + cap, -1);
     hmask = cap - 1;
   }
-  St &fresh(uint64_t key) {
-    nkeys.push_back(key);
-    nst.emplace_back();
-    St &s = nst.back();
-    memset(&s, 0, sizeof(St));
-    return s;
-  }
-  St &slot(uint64_t key) {
-    if (!merging) return fresh(key);
+  // the state of `key` and whether it already existed
+  St &slot(uint64_t key, bool &existed) {
+    existed = false;
+    if (!merging) { nkeys.push_back(key); nst.emplace_back(); return nst.back(); }
     for (size_t h = (key * 0x9E3779B97F4A7C15ull) >> 17;; ++h) {
       const size_t i = h & hmask;
       if (hval[i] < 0) {
         hkey[i] = key;
         hval[i] = int(nkeys.size());
-        return fresh(key);
+        nkeys.push_back(key);
+        nst.emplace_back();
+        return nst.back();
       }
-      if (hkey[i] == key) return nst[hval[i]];
+      if (hkey[i] == key) { existed = true; return nst[hval[i]]; }
     }
   }
-  // dst += F * src (F monomial with entries in {0, +-1, +-i})
+  // dst (+)= F * src (F monomial with entries in {0, +-1, +-i}); a new
+  // state is written, an existing one accumulated
   void push(const Mono &F, const St &src, uint64_t key) {
-    St &d = slot(key);
+    bool existed;
+    St &d = slot(key, existed);
+    if (!existed) {
+      for (int r = 0; r < 4; ++r) {
+        const double vr = double(F.val[r].real()), vi = double(F.val[r].imag());
+        const int c0 = F.col[r];
+        for (int c = 0; c < 4; ++c) {
+          const double x = src.re[c0][c], y = src.im[c0][c];
+          d.re[r][c] = vr * x - vi * y;
+          d.im[r][c] = vr * y + vi * x;
+        }
+      }
+      return;
+    }
     for (int r = 0; r < 4; ++r) {
       const long double vr = F.val[r].real(), vi = F.val[r].imag();
       const int c0 = F.col[r];
@@ -983,7 +994,11 @@ static void emit_term(Emitter &E, const TermInfo &T, const std::string &out, Gen
       for (auto &pr : pat) { int a = mom_items[pr.first], b = mom_items[pr.second]; D.pair_partner[a] = b; D.pair_partner[b] = a; }
       if (getenv("QED_GEN_DFS")) D.go(0, mono_identity(), -1, -1, 0u, -1);
       else {
-        DP Q;
+        // one recursion object per thread: its state buffers keep their
+        // capacity from run to run
+        static thread_local DP Q;
+        Q.acc.clear();
+        Q.mag.clear();
         Q.seq = D.seq; Q.proj = D.proj; Q.allow_p = D.allow_p; Q.allow_q = D.allow_q; Q.allow_k = D.allow_k;
         Q.slot_of_item = D.slot_of_item; Q.pair_partner = D.pair_partner;
         Q.run();
@@ -1114,25 +1129,39 @@ static qvm::Entry gen_vm_graph(const Graph &g, GenStats &st) {
 }
 
 // All graphs of order n, one per mirror pair (the smaller key; QED_VM_ALL=1:
-// both orientations), on all host threads; QED_VM_LIMIT=k keeps the first k.
-static void gen_vm_order(const std::string &dir, int n, GenStats &st) {
+// both orientations), or the listed ones, on all host threads;
+// QED_VM_LIMIT=k keeps the first k.
+static void gen_vm_order(const std::string &dir, int n, GenStats &st, const std::vector<int> &only) {
   std::vector<Graph> gs;
   const bool all = getenv("QED_VM_ALL") && atoi(getenv("QED_VM_ALL"));
-  for (auto &g : enumerate_graphs(n))
-    if (all || !(g.mirror().key() < g.key())) gs.push_back(g);
+  const auto every = enumerate_graphs(n);
+  if (!only.empty()) {
+    for (int i : only) {
+      if (i < 0 || size_t(i) >= every.size()) { fprintf(stderr, "qed_gen: graph index %d out of range\n", i); exit(1); }
+      gs.push_back(every[size_t(i)]);
+    }
+  } else {
+    for (auto &g : every)
+      if (all || !(g.mirror().key() < g.key())) gs.push_back(g);
+  }
   if (const char *lim = getenv("QED_VM_LIMIT")) {
     const size_t k = size_t(atol(lim));
     if (k < gs.size()) gs.resize(k);
   }
   std::vector<qvm::Entry> es(gs.size());
   std::vector<GenStats> sts(gs.size());
+  // largest graphs (most forest terms) first, so that no long one starts last
+  std::vector<size_t> order(gs.size());
+  std::vector<size_t> cost(gs.size());
+  for (size_t i = 0; i < gs.size(); ++i) { order[i] = i; cost[i] = build_terms(gs[i]).size(); }
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
   std::atomic<size_t> next{0};
   unsigned nt = std::max(1u, std::thread::hardware_concurrency());
   if (const char *j = getenv("QED_GEN_JOBS")) nt = std::max(1, atoi(j));
   std::vector<std::thread> th;
   for (unsigned t = 0; t < nt; ++t)
     th.emplace_back([&]() {
-      for (size_t i; (i = next.fetch_add(1)) < gs.size();) es[i] = gen_vm_graph(gs[i], sts[i]);
+      for (size_t k; (k = next.fetch_add(1)) < gs.size();) es[order[k]] = gen_vm_graph(gs[order[k]], sts[order[k]]);
     });
   for (auto &t : th) t.join();
   size_t ins = 0;
@@ -1169,9 +1198,17 @@ int main(int argc, char **argv) {
   GenStats st;
   for (int ai = 2; ai < argc; ++ai) {
     if (argv[ai][0] == 'v') {
-      // bytecode programs for the interpreter kernels: vm_n<n>.bin
+      // bytecode programs for the interpreter kernels: vm_n<n>.bin;
+      // "v<n>@<file>": only the graphs whose indices (in the full
+      // enumeration) the file lists
       const int n = atoi(argv[ai] + 1);
-      gen_vm_order(dir, n, st);
+      std::vector<int> only;
+      if (const char *at = strchr(argv[ai], '@')) {
+        std::ifstream in(at + 1);
+        if (!in) { fprintf(stderr, "qed_gen: cannot read %s\n", at + 1); return 1; }
+        for (int x; in >> x;) only.push_back(x);
+      }
+      gen_vm_order(dir, n, st, only);
       continue;
     }
     int n = atoi(argv[ai]);
@@ -1249,6 +1286,7 @@ int main(int argc, char **argv) {
       reg_lines.push_back(g.n_lines());
     }
   }
+  if (reg.empty()) return 0;              // bytecode orders only: the registry is the compiled set's
   std::ofstream f(dir + "/qed_registry.h");
   f << "// Generated by qed_gen. Registry of the generated integrands.\n#pragma once\n";
   f << "#define QED_N_GENERATED " << reg.size() << "\n";

@@ -201,6 +201,23 @@ class Compiler {
   // names of the forest-term outputs in summation order
   Program compile(const std::string &body, const std::vector<std::string> &terms) {
     parse(body, terms);
+    // drop values nothing uses (e.g. a line's C or K polynomial that no
+    // monomial needs): backward pass from the terms and the return
+    {
+      std::set<std::string> live;
+      std::vector<Stmt> kept;
+      for (size_t j = st.size(); j-- > 0;) {
+        const Stmt &S = st[j];
+        const bool keep = S.k == Stmt::TERM || S.k == Stmt::RET || live.count(S.lhs);
+        if (!keep) continue;
+        if (S.k == Stmt::DEF) live.erase(S.lhs);
+        std::vector<std::string> u;
+        collect_uses(S.rhs, u);
+        for (auto &n : u) live.insert(n);
+        kept.push_back(S);
+      }
+      st.assign(kept.rbegin(), kept.rend());
+    }
     // last use of every name (alias-resolved)
     std::map<std::string, size_t> last;
     for (size_t i = 0; i < st.size(); ++i) {

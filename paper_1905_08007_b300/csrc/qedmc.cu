@@ -27,6 +27,7 @@
 #include "qed_graph.hpp"
 #include "qed_kernels.cuh"
 #include "qed_batch.cuh"
+#include "qed_vm.cuh"
 #include "qed_registry.h"
 
 // ---------------------------------------------------------------------------
@@ -51,6 +52,9 @@ QED_GENERATED_LIST(QED_DECL_KSET)
 static const KernelSet *const g_kernels[] = {QED_GENERATED_LIST(QED_REF_KSET)};
 // persistent batched kernels (defined in the generated batch translation unit)
 extern const void *const qed_batch_kernels[2];
+// bytecode path: one kernel set per line count N = 3n
+static const VmKernelSet g_vm_kernels[QED_MAX_LOOPS] = {QED_VM_KSET(3), QED_VM_KSET(6), QED_VM_KSET(9),
+                                                        QED_VM_KSET(12), QED_VM_KSET(15)};
 
 // ---------------------------------------------------------------------------
 // host objects
@@ -72,6 +76,18 @@ struct qed_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk0 = nullptr, evk1 = nullptr;
   std::vector<double> h_partials;
   std::vector<unsigned long long> h_counts;
+  // bytecode integrands registered by qed_programs_load
+  struct VmProg {
+    std::string name;
+    int n_lines, n_regs, n_ins, n_kon;
+    double flops;
+    const uint32_t *d_ins;
+    const double *d_kon;
+  };
+  std::vector<VmProg> vm;
+  std::vector<void *> vm_bufs;
+  bool prefer_vm = false;
+  int vm_threads = 128;      // threads per block of the FP64 interpreter kernels
 };
 
 struct qed_diag {
@@ -79,6 +95,7 @@ struct qed_diag {
   qed::Graph g;
   uint32_t stream_id = 0;
   int fid = -1;
+  int vm = -1;                       // index of the bytecode program (fid = -1), or -1
   int N = 0;
   double logZ = 0.0;
   double d_min = 0.05;
@@ -150,14 +167,15 @@ static int ensure_scratch(qed_ctx *c, int blocks) {
 }
 
 extern "C" int qed_ctx_create(int device, uint64_t flags, qed_ctx **out) {
-  (void)flags;
   if (!out) return set_err(QED_EINVAL, "out is NULL");
+  if (flags & ~uint64_t(QED_CTX_PREFER_PROGRAMS)) return set_err(QED_EINVAL, "unknown context flags");
   int ndev = 0;
   CUDA_TRY(cudaGetDeviceCount(&ndev));
   if (device < 0 || device >= ndev) return set_err(QED_EINVAL, "no such device");
   CUDA_TRY(cudaSetDevice(device));
   qed_ctx *c = new qed_ctx();
   c->device = device;
+  c->prefer_vm = (flags & QED_CTX_PREFER_PROGRAMS) != 0;
   cudaDeviceProp prop;
   CUDA_TRY(cudaGetDeviceProperties(&prop, device));
   c->sms = prop.multiProcessorCount;
@@ -184,6 +202,7 @@ extern "C" int qed_ctx_destroy(qed_ctx *c) {
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->evk0) cudaEventDestroy(c->evk0);
   if (c->evk1) cudaEventDestroy(c->evk1);
+  for (void *p : c->vm_bufs) cudaFree(p);
   delete c;
   return QED_OK;
 }
@@ -206,6 +225,97 @@ extern "C" int qed_ctx_set_launch(qed_ctx *c, int threads, int blocks) {
 extern "C" int qed_ctx_set_threshold(qed_ctx *c, double rel) {
   if (!c || !(rel > 0.0)) return set_err(QED_EINVAL, "threshold must be > 0");
   c->thresh = rel;
+  return QED_OK;
+}
+
+// ---------------------------------------------------------------------------
+// bytecode programs
+// ---------------------------------------------------------------------------
+// Every instruction is checked against its program's register and constant
+// counts here, so that the interpreter's shared-memory accesses stay inside
+// the frame the host sized for it.
+static bool vm_check(const uint32_t *ins, int n_ins, int n_regs, int n_kon, int n_lines, std::string &why) {
+  if (n_regs < n_lines || n_regs > 512 || n_kon < 0 || n_kon > 512 || n_ins < 1) { why = "program sizes out of range"; return false; }
+  auto ok = [&](uint32_t a) { return a < VM_KFLAG ? int(a) < n_regs : int(a - VM_KFLAG) < n_kon; };
+  bool ended = false;
+  for (int i = 0; i < n_ins; ++i) {
+    const uint32_t w = ins[i], op = w & 15u, a = (w >> 4) & 1023u, b = (w >> 14) & 1023u;
+    if (w >> 24) { why = "reserved instruction bits set"; return false; }
+    switch (op) {
+      case VM_END: ended = true; break;
+      case VM_LD: case VM_ADD: case VM_MUL: if (!ok(a)) { why = "operand out of range"; return false; } break;
+      case VM_FMA: case VM_FMAC: case VM_ACCW: case VM_LDMUL:
+        if (!ok(a) || !ok(b)) { why = "operand out of range"; return false; } break;
+      case VM_RCP: case VM_ABS: break;
+      case VM_ST: if (a >= VM_KFLAG || int(a) >= n_regs || int(a) < n_lines) { why = "store target out of range"; return false; } break;
+      default: why = "unknown opcode"; return false;
+    }
+    if (ended) break;
+  }
+  if (!ended) { why = "program without END"; return false; }
+  return true;
+}
+
+extern "C" int qed_programs_load(qed_ctx *c, const void *data, size_t bytes, int *count) {
+  if (!c || !data) return set_err(QED_EINVAL, "ctx/data is NULL");
+  const unsigned char *p = static_cast<const unsigned char *>(data), *end = p + bytes;
+  if (bytes < 16 || std::memcmp(p, "QEDVM001", 8) != 0) return set_err(QED_EINVAL, "not a qed program file");
+  uint32_t n = 0;
+  std::memcpy(&n, p + 8, 4);
+  p += 16;
+  struct Rec { qed_ctx::VmProg pr; const uint32_t *ins; const double *kon; };
+  std::vector<Rec> recs;
+  size_t words = 0, kons = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    if (end - p < 64 + 24) return set_err(QED_EINVAL, "truncated program file");
+    Rec r;
+    char nm[65] = {0};
+    std::memcpy(nm, p, 64);
+    r.pr.name = nm;
+    int32_t m[4];
+    std::memcpy(m, p + 64, 16);
+    std::memcpy(&r.pr.flops, p + 80, 8);
+    p += 88;
+    r.pr.n_lines = m[0]; r.pr.n_regs = m[1]; r.pr.n_ins = m[2]; r.pr.n_kon = m[3];
+    if (m[0] < 3 || m[0] > 3 * QED_MAX_LOOPS || m[0] % 3 || m[2] < 1 || m[3] < 0) return set_err(QED_EINVAL, "bad program header");
+    const size_t ib = (size_t(m[2]) + (m[2] & 1)) * 4, kb = size_t(m[3]) * 8;
+    if (size_t(end - p) < ib + kb) return set_err(QED_EINVAL, "truncated program file");
+    r.ins = reinterpret_cast<const uint32_t *>(p);
+    r.kon = reinterpret_cast<const double *>(p + ib);
+    std::string why;
+    std::vector<uint32_t> tmp(r.ins, r.ins + m[2]);
+    if (!vm_check(tmp.data(), m[2], m[1], m[3], m[0], why)) return set_err(QED_EINVAL, "program " + r.pr.name + ": " + why);
+    p += ib + kb;
+    words += (size_t(m[2]) + 3) & ~size_t(3);
+    kons += size_t(m[3]);
+    recs.push_back(r);
+  }
+  CUDA_TRY(cudaSetDevice(c->device));
+  // one buffer per file: instruction words (each program END-padded to a
+  // multiple of 4 words, 16-byte aligned), then the constants
+  void *buf = nullptr;
+  // 16 spare bytes at the end: the interpreter loads the instruction group
+  // after the current one before executing it, so the last program's END
+  // group is followed by at least 16 readable bytes
+  const size_t wbytes = words * 4, total = wbytes + kons * 8 + 16;
+  CUDA_TRY(cudaMalloc(&buf, total));
+  std::vector<unsigned char> host(total, 0);
+  size_t wo = 0, ko = wbytes;
+  std::vector<qed_ctx::VmProg> progs;
+  for (auto &r : recs) {
+    std::memcpy(host.data() + wo, r.ins, size_t(r.pr.n_ins) * 4);
+    r.pr.d_ins = reinterpret_cast<const uint32_t *>(static_cast<unsigned char *>(buf) + wo);
+    wo += ((size_t(r.pr.n_ins) + 3) & ~size_t(3)) * 4;
+    std::memcpy(host.data() + ko, r.kon, size_t(r.pr.n_kon) * 8);
+    r.pr.d_kon = reinterpret_cast<const double *>(static_cast<unsigned char *>(buf) + ko);
+    ko += size_t(r.pr.n_kon) * 8;
+    progs.push_back(r.pr);
+  }
+  cudaError_t e = cudaMemcpy(buf, host.data(), total, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { cudaFree(buf); return set_err(QED_ECUDA, cudaGetErrorString(e)); }
+  c->vm_bufs.push_back(buf);
+  for (auto &pr : progs) c->vm.push_back(pr);
+  if (count) *count = int(progs.size());
   return QED_OK;
 }
 
@@ -271,14 +381,18 @@ extern "C" int qed_diagram_load(qed_ctx *ctx, const qed_graph *gin, const qed_pd
   qed::Graph g;
   std::string why;
   if (!to_graph(gin, g, why)) return set_err(QED_EINVAL, why);
-  int fid = -1;
+  int fid = -1, vm = -1;
   const std::string nm = g.name();
   for (int i = 0; i < QED_N_GENERATED; ++i) if (nm == qed_generated_names[i]) fid = i;
-  if (fid < 0) return set_err(QED_ENOTFOUND, "no generated integrand for " + nm);
+  if (fid < 0 || ctx->prefer_vm)
+    for (size_t i = 0; i < ctx->vm.size(); ++i)
+      if (ctx->vm[i].name == nm && ctx->vm[i].n_lines == g.n_lines()) vm = int(i);
+  if (vm >= 0) fid = -1;
+  if (fid < 0 && vm < 0) return set_err(QED_ENOTFOUND, "no generated integrand or program for " + nm);
   const int N = g.n_lines();
   const size_t M = size_t(1) << N;
   qed_diag *d = new qed_diag();
-  d->ctx = ctx; d->g = g; d->stream_id = gin->stream_id; d->fid = fid; d->N = N;
+  d->ctx = ctx; d->g = g; d->stream_id = gin->stream_id; d->fid = fid; d->vm = vm; d->N = N;
   if (pdf && pdf->deg) {
     d->deg0.assign(pdf->deg, pdf->deg + M);
     for (size_t m = 1; m + 1 < M; ++m)
@@ -315,7 +429,7 @@ extern "C" int qed_diagram_free(qed_diag *d) {
 extern "C" int qed_diagram_info(const qed_diag *d, int *n_lines, int *fid, double *log_norm) {
   if (!d) return set_err(QED_EINVAL, "diag is NULL");
   if (n_lines) *n_lines = d->N;
-  if (fid) *fid = d->fid;
+  if (fid) *fid = d->vm >= 0 ? QED_N_GENERATED + d->vm : d->fid;
   if (log_norm) *log_norm = d->logZ;
   return QED_OK;
 }
@@ -338,6 +452,88 @@ static KParams base_params(const qed_diag *d, uint64_t begin, uint64_t n, uint64
 
 static int launch(const void *fn, int blocks, int threads, size_t smem, cudaStream_t st, void **args) {
   CUDA_TRY(cudaLaunchKernel(fn, dim3(blocks), dim3(threads), args, smem, st));
+  return QED_OK;
+}
+
+// Launch shape of an interpreter kernel: the block size starts at `threads`
+// and halves until the frame (constants + one register file per thread)
+// fits in shared memory; blocks = resident blocks per SM x SMs.
+struct VmLaunch {
+  int threads = 0, blocks = 0;
+  size_t smem = 0;
+  VmCode code;
+};
+static int vm_launch(const qed_ctx *c, const qed_ctx::VmProg &pr, const void *fn, bool dd_frame, int threads,
+                     VmLaunch &L) {
+  L.code = VmCode{pr.d_ins, pr.d_kon, pr.n_kon, pr.n_regs};
+  const size_t cap = 220 * 1024;       // dynamic part; the kernels' static shared memory is a few KB
+  auto bytes = [&](int t) {
+    return dd_frame ? vm_smem_bytes<dd>(pr.n_kon, pr.n_regs, t) : vm_smem_bytes<double>(pr.n_kon, pr.n_regs, t);
+  };
+  int T = threads;
+  while (T > 32 && bytes(T) > cap) T /= 2;
+  if (bytes(T) > cap) return set_err(QED_EINVAL, "program " + pr.name + " needs more shared memory than a block has");
+  L.threads = T;
+  L.smem = bytes(T);
+  CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L.smem)));
+  int occ = 0;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, T, L.smem));
+  L.blocks = std::max(1, occ) * c->sms;
+  return QED_OK;
+}
+static const VmKernelSet &vm_kernels(const qed_diag *d) { return g_vm_kernels[d->N / 3 - 1]; }
+
+static int fold(qed_ctx *c, int blocks, qed_result *r, bool add_flagged_as_count);
+static void finish(qed_result *r);
+
+// Per-graph integration with a bytecode integrand: launches of at most
+// queue_cap samples, so the flagged queue cannot overflow.
+static int integrate_range_vm(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed, qed_result *out) {
+  qed_ctx *c = d->ctx;
+  const VmKernelSet &K = vm_kernels(d);
+  const auto &pr = c->vm[d->vm];
+  VmLaunch L1, L2;
+  int rc = vm_launch(c, pr, K.integrate, false, c->vm_threads, L1);
+  if (!rc) rc = vm_launch(c, pr, K.redo, true, 64, L2);
+  if (!rc) rc = ensure_scratch(c, std::max(L1.blocks, L2.blocks));
+  if (rc) return rc;
+  qed_result r;
+  std::memset(&r, 0, sizeof r);
+  r.n = n;
+  CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+  const uint64_t chunk = c->queue_cap;
+  for (uint64_t off = 0; off < n; off += chunk) {
+    const uint64_t m = std::min(chunk, n - off);
+    KParams P = base_params(d, begin + off, m, seed);
+    P.partials = c->partials; P.counts = c->counts;
+    P.queue = c->queue; P.queue_len = c->queue_len; P.queue_cap = c->queue_cap;
+    CUDA_TRY(cudaMemsetAsync(c->queue_len, 0, sizeof(unsigned int), c->stream));
+    void *args[] = {&P, &L1.code};
+    CUDA_TRY(cudaEventRecord(c->evk0, c->stream));
+    if ((rc = launch(K.integrate, L1.blocks, L1.threads, L1.smem, c->stream, args))) return rc;
+    CUDA_TRY(cudaEventRecord(c->evk1, c->stream));
+    ++r.launches;
+    if ((rc = fold(c, L1.blocks, &r, true))) return rc;
+    float kms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&kms, c->evk0, c->evk1));
+    r.kernel_seconds += kms * 1e-3;
+    unsigned int qn = 0;
+    CUDA_TRY(cudaMemcpy(&qn, c->queue_len, sizeof qn, cudaMemcpyDeviceToHost));
+    if (qn > c->queue_cap) return set_err(QED_ECUDA, "flagged queue overflow");   // cannot happen: m <= queue_cap
+    if (qn > 0) {
+      void *args2[] = {&P, &L2.code, &qn};
+      if ((rc = launch(K.redo, L2.blocks, L2.threads, L2.smem, c->stream, args2))) return rc;
+      ++r.launches;
+      if ((rc = fold(c, L2.blocks, &r, false))) return rc;
+    }
+  }
+  CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+  CUDA_TRY(cudaEventSynchronize(c->ev1));
+  float ms = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  r.seconds = ms * 1e-3;
+  finish(&r);
+  *out = r;
   return QED_OK;
 }
 
@@ -377,6 +573,7 @@ extern "C" int qed_integrate_range(qed_diag *d, uint64_t begin, uint64_t n, uint
   if (!d || !out) return set_err(QED_EINVAL, "diag/out is NULL");
   qed_ctx *c = d->ctx;
   CUDA_TRY(cudaSetDevice(c->device));
+  if (d->vm >= 0) return integrate_range_vm(d, begin, n, seed, out);
   const KernelSet &K = *g_kernels[d->fid];
   const int threads = c->threads;
   const int blocks = c->blocks > 0 ? c->blocks : 4 * c->sms;
@@ -435,6 +632,16 @@ extern "C" int qed_dump_points(qed_diag *d, uint64_t begin, uint64_t n, uint64_t
   CUDA_TRY(cudaSetDevice(c->device));
   KParams P = base_params(d, begin, n, seed);
   P.z_out = z_dev; P.f_out = f_dev; P.lp_out = lp_dev; P.flag_out = flag_dev;
+  if (d->vm >= 0) {
+    VmLaunch L;
+    int rc = vm_launch(c, c->vm[d->vm], vm_kernels(d).dump, false, c->vm_threads, L);
+    if (rc) return rc;
+    const int blocks = int(std::max<uint64_t>(1, std::min<uint64_t>((n + L.threads - 1) / L.threads, uint64_t(L.blocks))));
+    void *args[] = {&P, &L.code};
+    if ((rc = launch(vm_kernels(d).dump, blocks, L.threads, L.smem, c->stream, args))) return rc;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return QED_OK;
+  }
   const int threads = c->threads;
   const int blocks = int(std::max<uint64_t>(1, std::min<uint64_t>((n + threads - 1) / threads, uint64_t(c->sms) * 8)));
   void *args[] = {&P};
@@ -448,6 +655,17 @@ extern "C" int qed_eval_points(qed_diag *d, const double *z_dev, uint64_t n, int
   if (!d || !z_dev || !f_dev || (prec != 0 && prec != 1)) return set_err(QED_EINVAL, "bad argument");
   qed_ctx *c = d->ctx;
   CUDA_TRY(cudaSetDevice(c->device));
+  if (d->vm >= 0) {
+    VmLaunch L;
+    const void *fn = vm_kernels(d).eval;
+    int rc = vm_launch(c, c->vm[d->vm], fn, prec == 1, prec == 1 ? 64 : c->vm_threads, L);
+    if (rc) return rc;
+    const int blocks = int(std::max<uint64_t>(1, std::min<uint64_t>((n + L.threads - 1) / L.threads, uint64_t(L.blocks))));
+    void *args[] = {(void *)&z_dev, &n, &prec, &f_dev, &L.code};
+    if ((rc = launch(fn, blocks, L.threads, L.smem, c->stream, args))) return rc;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return QED_OK;
+  }
   const int threads = c->threads;
   const int blocks = int(std::max<uint64_t>(1, std::min<uint64_t>((n + threads - 1) / threads, uint64_t(c->sms) * 8)));
   void *args[] = {(void *)&z_dev, &n, &prec, &f_dev};
@@ -487,7 +705,7 @@ extern "C" int qed_diagram_flops(const qed_diag *d, double *flops) {
   // exp, density update), weight (exp, product), accumulation (square and
   // two compensated sums)
   const double sampler = 4.0 * (N - 1) + (N - 1) + (N - 1) * (N + 2) / 4.0 + 6.0 * (N - 1) + 2.0 + 9.0;
-  *flops = qed_generated_flops[d->fid] + sampler;
+  *flops = (d->vm >= 0 ? d->ctx->vm[d->vm].flops : qed_generated_flops[d->fid]) + sampler;
   return QED_OK;
 }
 
@@ -569,10 +787,36 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
   // items per round (all rounds the same size so one captured graph serves all)
   const uint64_t per_round = (total + rounds - 1) / rounds;
   const unsigned int n_items = unsigned(std::max<uint64_t>(uint64_t(k), (per_round + chunk - 1) / chunk));
-  const uint32_t list_cap = uint32_t(std::max<uint64_t>(1, chunk / list_div));
+  // a batch is all compiled graphs or all bytecode graphs of one loop order
+  int nvm = 0;
+  for (int g = 0; g < k; ++g) nvm += d[g]->vm >= 0;
+  const bool vmb = nvm > 0;
+  if (vmb && nvm != k) return set_err(QED_EINVAL, "a batch holds compiled graphs or bytecode graphs, not both");
+  if (vmb)
+    for (int g = 0; g < k; ++g)
+      if (d[g]->N != d[0]->N) return set_err(QED_EINVAL, "a batch of bytecode graphs holds one loop order");
+  // bytecode batches: the flagged list of an item holds the whole chunk
+  const uint32_t list_cap = vmb ? uint32_t(chunk) : uint32_t(std::max<uint64_t>(1, chunk / list_div));
   int Nmax = 0;
   for (int g = 0; g < k; ++g) Nmax = std::max(Nmax, d[g]->N);
-  const size_t smem = table_smem(Nmax);
+  size_t smem = table_smem(Nmax), smem2 = smem;
+  int thr1 = 256, thr2 = 256;
+  const void *kern1 = qed_batch_kernels[0], *kern2 = qed_batch_kernels[1];
+  VmLaunch L1, L2;
+  if (vmb) {
+    qed_ctx::VmProg big = c->vm[d[0]->vm];
+    for (int g = 0; g < k; ++g) {
+      big.n_regs = std::max(big.n_regs, c->vm[d[g]->vm].n_regs);
+      big.n_kon = std::max(big.n_kon, c->vm[d[g]->vm].n_kon);
+    }
+    const VmKernelSet &K = vm_kernels(d[0]);
+    kern1 = K.batch64;
+    kern2 = K.batchdd;
+    int rc = vm_launch(c, big, kern1, false, c->vm_threads, L1);
+    if (!rc) rc = vm_launch(c, big, kern2, true, 64, L2);
+    if (rc) return rc;
+    smem = L1.smem; smem2 = L2.smem; thr1 = L1.threads; thr2 = L2.threads;
+  }
   // device and pinned buffers
   DevBuf dd_diags, dd_items, dd_next, dd_part, dd_cnt, dd_lists, dd_pdd, dd_cdd;
   HostBuf h_items, h_out;
@@ -592,6 +836,11 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
     const size_t M = size_t(1) << d[g]->N;
     hd[g].F = d[g]->d_tab; hd[g].G = d[g]->d_tab + M; hd[g].inv = d[g]->d_tab + 2 * M; hd[g].off = d[g]->d_tab + 3 * M;
     hd[g].logZ = d[g]->logZ; hd[g].stream = d[g]->stream_id; hd[g].fid = d[g]->fid; hd[g].N = d[g]->N; hd[g].pad = 0;
+    hd[g].vins = nullptr; hd[g].vkon = nullptr; hd[g].vnk = 0; hd[g].vnr = 0;
+    if (d[g]->vm >= 0) {
+      const auto &pr = c->vm[d[g]->vm];
+      hd[g].vins = pr.d_ins; hd[g].vkon = pr.d_kon; hd[g].vnk = pr.n_kon; hd[g].vnr = pr.n_regs;
+    }
   }
   CUDA_TRY(cudaMemcpy(dd_diags.p, hd.data(), sizeof(BatchDiag) * k, cudaMemcpyHostToDevice));
   BatchParams B;
@@ -601,9 +850,9 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
   B.lists = (uint32_t *)dd_lists.p; B.list_cap = list_cap;
   B.part_dd = (double *)dd_pdd.p; B.cnt_dd = (unsigned long long *)dd_cdd.p;
   int occ = 0;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)qed_batch_kernels[0], 256, smem));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern1, thr1, smem));
   const int grid1 = std::max(1, occ) * c->sms;
-  const int grid2 = std::min<int>(int(n_items), 4 * c->sms);
+  const int grid2 = std::min<int>(int(n_items), vmb ? L2.blocks : 4 * c->sms);
   // host-side layout of the pinned output block
   double *o_part = (double *)h_out.p;
   double *o_pdd = o_part + 4 * size_t(n_items);
@@ -617,9 +866,9 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
     // after every replay
     const unsigned int evflags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     CUDA_TRY(cudaEventRecordWithFlags(c->evk0, st, evflags));
-    CUDA_TRY(cudaLaunchKernel(qed_batch_kernels[0], dim3(grid1), dim3(256), args, smem, st));
+    CUDA_TRY(cudaLaunchKernel(kern1, dim3(grid1), dim3(thr1), args, smem, st));
     CUDA_TRY(cudaEventRecordWithFlags(c->evk1, st, evflags));
-    CUDA_TRY(cudaLaunchKernel(qed_batch_kernels[1], dim3(grid2), dim3(256), args, smem, st));
+    CUDA_TRY(cudaLaunchKernel(kern2, dim3(grid2), dim3(thr2), args, smem2, st));
     CUDA_TRY(cudaMemcpyAsync(o_part, dd_part.p, sizeof(double) * 4 * n_items, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(o_pdd, dd_pdd.p, sizeof(double) * 4 * n_items, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(o_cnt, dd_cnt.p, sizeof(unsigned long long) * 2 * n_items, cudaMemcpyDeviceToHost, st));
@@ -778,13 +1027,22 @@ extern "C" int qed_pdf_grad(qed_diag *d, uint64_t begin, uint64_t n, uint64_t se
   qed_ctx *c = d->ctx;
   CUDA_TRY(cudaSetDevice(c->device));
   const int N = d->N;
-  const int blocks = 4 * c->sms, threads = 256;
+  int blocks = 4 * c->sms, threads = 256;
+  VmLaunch L;
+  if (d->vm >= 0) {
+    int rc = vm_launch(c, c->vm[d->vm], vm_kernels(d).grad, false, c->vm_threads, L);
+    if (rc) return rc;
+    blocks = L.blocks;
+    threads = L.threads;
+  }
   double *dout = nullptr;
   CUDA_TRY(cudaMalloc(&dout, sizeof(double) * blocks * (2 * N + 1)));
   KParams P = base_params(d, begin, n, seed);
   const uint8_t *act = d->d_act;
   void *args[] = {&P, (void *)&act, &dout};
-  int rc = launch(g_kernels[d->fid]->grad, blocks, threads, table_smem(N), c->stream, args);
+  void *vargs[] = {&P, &L.code, (void *)&act, &dout};
+  int rc = d->vm >= 0 ? launch(vm_kernels(d).grad, blocks, threads, L.smem, c->stream, vargs)
+                      : launch(g_kernels[d->fid]->grad, blocks, threads, table_smem(N), c->stream, args);
   std::vector<double> h(size_t(blocks) * (2 * N + 1));
   if (!rc) {
     cudaError_t e = cudaMemcpyAsync(h.data(), dout, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
@@ -933,6 +1191,7 @@ static int noalloc_scratch(int device, NoAllocScratch **out) {
 extern "C" int qed_integrate_range_noalloc(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed, qed_result *out) {
   if (!d || !out) return set_err(QED_EINVAL, "diag/out is NULL");
   qed_ctx *c = d->ctx;
+  if (d->vm >= 0) return set_err(QED_EINVAL, "qed_integrate_range_noalloc: compiled integrands only (this graph uses a bytecode program)");
   const int threads = c->threads;
   const int blocks = c->blocks > 0 ? c->blocks : 4 * c->sms;
   if (blocks > QED_NOALLOC_MAX_BLOCKS)

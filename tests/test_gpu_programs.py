@@ -1,0 +1,165 @@
+"""Bytecode integrands on the GPU (the interpreter kernels), through the C ABI.
+
+* Two and three loops: the same graph with its compiled integrand and with
+  its program (a QED_CTX_PREFER_PROGRAMS context) gives bit-identical Eq. (1)
+  points and densities, and integrand values equal within both paths'
+  rounding-error estimate, in FP64 and double-double; integrations and the
+  adjoint of the second moment agree.
+* Four loops (12 lines, 11-dim simplex; no compiled integrands exist): per
+  point parity with the oracle's long-double values stored by
+  tests/golden/make_four_loop.py at the points of fixed Philox counters, and
+  a batched, deterministic integration of a set of graphs.
+"""
+import math
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1905_08007_b300 as q                      # noqa: E402
+
+ROOT = Path(__file__).resolve().parents[1]
+GOLDEN4 = ROOT / "tests" / "golden" / "four_loop_points.txt"
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+@pytest.fixture(scope="module")
+def ctxs():
+    _need_gpu()
+    comp = q.Context(0, threshold=1e-12)
+    vm = q.Context(0, threshold=1e-12, prefer_programs=True)
+    if vm.n_programs == 0:
+        pytest.skip("no program files built")
+    return comp, vm
+
+
+def _pairs(n, idx):
+    gs = q.enumerate_graphs(n)
+    red = {(g.pairs, g.e) for g in q.enumerate_graphs(n, reduced=True)}
+    return [gs[i] for i in idx if (gs[i].pairs, gs[i].e) in red]
+
+
+@pytest.mark.parametrize("n,idx", [(2, range(6)), (3, [0, 9, 19, 29, 39])])
+def test_programs_match_compiled_points(ctxs, n, idx):
+    comp, vm = ctxs
+    for g in _pairs(n, idx):
+        dc, dv = comp.load(g), vm.load(g)
+        assert dv.integrand_id != dc.integrand_id
+        zc, fc, lpc, flc = dc.dump_points(5, 3000, seed=3)
+        zv, fv, lpv, flv = dv.dump_points(5, 3000, seed=3)
+        assert torch.equal(zc, zv) and torch.equal(lpc, lpv)
+        fc, fv = fc.cpu().numpy(), fv.cpu().numpy()
+        ok = (flc.cpu().numpy() == 0) & (flv.cpu().numpy() == 0)
+        assert ok.mean() > 0.9
+        rel = np.abs(fv - fc)[ok] / np.abs(fc[ok])
+        assert rel.max() < 4e-12, rel.max()
+        # double-double at the same points
+        gc = dc.eval_points(zc, prec=1).cpu().numpy()
+        gv = dv.eval_points(zc, prec=1).cpu().numpy()
+        assert np.max(np.abs(gv - gc) / np.abs(gc)) < 1e-13
+        # FP64 evaluation at caller points equals the dump's values
+        ev = dv.eval_points(zc, prec=0).cpu().numpy()
+        np.testing.assert_array_equal(ev, fv)
+
+
+def test_programs_match_compiled_integration(ctxs):
+    comp, vm = ctxs
+    g = q.enumerate_graphs(2)[1]
+    rc = comp.load(g).integrate(1 << 22, seed=11)
+    rv = vm.load(g).integrate(1 << 22, seed=11)
+    assert rc.n == rv.n
+    assert rv.value == pytest.approx(rc.value, rel=1e-9)
+    assert rv.variance == pytest.approx(rc.variance, rel=1e-6)
+    assert abs(rv.n_flagged - rc.n_flagged) <= max(8, rc.n_flagged // 50)
+
+
+def test_programs_match_compiled_adjoint(ctxs):
+    comp, vm = ctxs
+    from paper_1905_08007_b300 import _lib
+    g = q.enumerate_graphs(2)[2]
+    out = []
+    for c in (comp, vm):
+        d = c.load(g)
+        N = d.n_lines
+        grad = (_lib.C.c_double * (2 * N))()
+        m2 = _lib.C.c_double()
+        _lib._check(_lib.load_library().qed_pdf_grad(d._h, 0, 1 << 20, 5, _lib.C.byref(m2), grad))
+        out.append((m2.value, np.array(list(grad))))
+    assert out[1][0] == pytest.approx(out[0][0], rel=1e-9)
+    np.testing.assert_allclose(out[1][1], out[0][1], rtol=1e-7, atol=1e-9 * np.abs(out[0][1]).max())
+
+
+def _golden4():
+    rows = [ln.split() for ln in GOLDEN4.read_text().splitlines() if ln and not ln.startswith("#")]
+    byg = {}
+    for r in rows:
+        byg.setdefault(int(r[0]), []).append(r)
+    return byg
+
+
+@pytest.fixture(scope="module")
+def ctx4():
+    _need_gpu()
+    c = q.Context(0, threshold=1e-12)
+    try:
+        c.load(q.enumerate_graphs(4)[85])
+    except q.QedError as e:
+        if e.code == -6:
+            pytest.skip("no four-loop programs built")
+        raise
+    return c
+
+
+def test_four_loop_points_match_oracle(ctx4):
+    if not GOLDEN4.exists():
+        pytest.skip("four_loop_points.txt not written")
+    gs = q.enumerate_graphs(4)
+    for gi, rs in _golden4().items():
+        d = ctx4.load(gs[gi])
+        assert d.n_lines == 12
+        ctrs = [int(r[1]) for r in rs]
+        zs, fs, lps, fls = [], [], [], []
+        for c in ctrs:
+            z, f, lp, fl = d.dump_points(c, 1, seed=0)
+            zs.append(z.cpu().numpy()[0]); fs.append(f.item()); lps.append(lp.item()); fls.append(fl.item())
+        z = np.array(zs)
+        zo = np.array([[float(v) for v in r[3:15]] for r in rs])
+        lpo = np.array([float(r[2]) for r in rs])
+        fo = np.array([float(np.longdouble(r[15])) for r in rs])
+        np.testing.assert_allclose(z, zo, rtol=1e-12, atol=0)
+        np.testing.assert_allclose(lps, lpo, rtol=1e-12, atol=1e-12)
+        # unflagged points (FP64 estimate within 1e-12, so condition number
+        # below ~1e3): the FP64 value, the double-double value and the
+        # long-double oracle agree to 1e-12; at flagged points the oracle's
+        # own long-double error grows with the condition number, so only
+        # rough agreement of the double-double value is required there
+        ok = np.array(fls) == 0
+        assert ok.sum() >= len(ok) // 2
+        rel = np.abs(np.array(fs) - fo) / np.abs(fo)
+        assert np.all(rel[ok] < 4e-12), (gi, rel)
+        fdd = d.eval_points(torch.tensor(zo, device="cuda"), prec=1).cpu().numpy()
+        rdd = np.abs(fdd - fo) / np.abs(fo)
+        assert np.all(rdd[ok] < 1e-12) and np.all(rdd < 1e-6), (gi, rdd)
+
+
+def test_four_loop_batch_deterministic(ctx4):
+    gs = q.enumerate_graphs(4, reduced=True)
+    ds = [ctx4.load(g) for g in gs[::34]]
+    kw = dict(rounds=2, chunk=1 << 13)
+    r1 = ctx4.integrate_batch(ds, 1 << 19, seed=2, **kw)
+    r2 = ctx4.integrate_batch(ds, 1 << 19, seed=2, **kw)
+    assert sum(r.n for r in r1) >= 1 << 19
+    for a, b in zip(r1, r2):
+        assert a.n > 0 and math.isfinite(a.value) and math.isfinite(a.variance)
+        assert a.sum_w == b.sum_w and a.sum_w2 == b.sum_w2 and a.n_flagged == b.n_flagged
+    # each graph's batch result equals its per-graph integration of the same counters
+    d0, r0 = ds[0], r1[0]
+    rp = d0.integrate(r0.n, seed=2)
+    assert rp.value == pytest.approx(r0.value, rel=1e-9, abs=1e-12)

@@ -1,0 +1,159 @@
+"""Bytecode integrands (the generator's program files for the interpreter
+kernels), checked on the CPU: every program is well formed, and a plain
+numpy interpretation of it reproduces the oracle's subtracted integrand
+(Sec. 2) at two, three and four loops.  At four loops the reference values
+are the oracle's, stored by tests/golden/make_four_loop.py at the Eq. (1)
+points of fixed Philox counters.
+
+Instruction word: op[0:4) a[4:14) b[14:24); operand >= 512 selects a
+constant.  Ops: END LD ADD MUL FMA(acc*a+b) FMAC(a*b+acc) RCP ABS ST ACCW
+LDMUL, in that order."""
+import struct
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from oracle.graphs import enumerate_graphs as o_enum
+from oracle.integrand import Integrand
+
+ROOT = Path(__file__).resolve().parents[1]
+GEN = ROOT / "paper_1905_08007_b300" / "csrc" / "_gen"
+GOLDEN4 = ROOT / "tests" / "golden" / "four_loop_points.txt"
+
+
+def read_programs(path):
+    data = path.read_bytes()
+    assert data[:8] == b"QEDVM001"
+    (count,) = struct.unpack_from("<I", data, 8)
+    off = 16
+    progs = {}
+    for _ in range(count):
+        name = data[off:off + 64].split(b"\0")[0].decode()
+        n_lines, n_regs, n_ins, n_kon = struct.unpack_from("<4i", data, off + 64)
+        (flops,) = struct.unpack_from("<d", data, off + 80)
+        off += 88
+        ins = np.frombuffer(data, dtype="<u4", count=n_ins, offset=off)
+        off += 4 * (n_ins + (n_ins & 1))
+        kon = np.frombuffer(data, dtype="<f8", count=n_kon, offset=off)
+        off += 8 * n_kon
+        progs[name] = dict(n_lines=n_lines, n_regs=n_regs, ins=ins, kon=kon, flops=flops)
+    assert off == len(data)
+    return progs
+
+
+def interpret(p, z, dtype=np.float64):
+    """acc / register machine of the generator, vectorised over points."""
+    z = np.asarray(z, dtype=dtype)
+    B, N = z.shape
+    R = np.zeros((p["n_regs"], B), dtype=dtype)
+    E = np.zeros((p["n_regs"], B), dtype=dtype)
+    R[:N] = z.T
+    E[:N] = np.abs(z.T)
+    K = p["kon"].astype(dtype)
+    acc = np.zeros(B, dtype=dtype)
+    ae = np.zeros(B, dtype=dtype)
+    W = np.zeros(B, dtype=dtype)
+
+    def get(x):
+        return (K[x - 512], abs(K[x - 512])) if x >= 512 else (R[x], E[x])
+
+    for w in p["ins"].tolist():
+        op, a, b = w & 15, (w >> 4) & 1023, (w >> 14) & 1023
+        if op == 0:
+            return acc, W
+        if op == 1:
+            v, e = get(a); acc = np.broadcast_to(v, (B,)).astype(dtype); ae = np.broadcast_to(e, (B,)).astype(dtype)
+        elif op == 2:
+            v, e = get(a); acc = acc + v; ae = ae + e
+        elif op == 3:
+            v, e = get(a); acc = acc * v; ae = ae * e
+        elif op == 4:
+            (v, e), (u, f) = get(a), get(b); acc = acc * v + u; ae = ae * e + f
+        elif op == 5:
+            (v, e), (u, f) = get(a), get(b); acc = v * u + acc; ae = e * f + ae
+        elif op == 6:
+            acc = 1 / acc; ae = np.abs(acc)
+        elif op == 7:
+            ae = np.abs(acc)
+        elif op == 8:
+            R[a] = acc; E[a] = ae
+        elif op == 9:
+            (v, e), (u, f) = get(a), get(b); W = W + np.abs(v) * f
+        elif op == 10:
+            (v, e), (u, f) = get(a), get(b); acc = v * u; ae = e * f
+        else:
+            raise AssertionError(f"bad opcode {op}")
+    raise AssertionError("program without END")
+
+
+def _name(g):
+    return f"n{g.n}_e{g.e}" + "".join(f"_{s}{t}" for s, t in g.pairs)
+
+
+def _programs(n):
+    path = GEN / f"vm_n{n}.bin"
+    if not path.exists():
+        pytest.skip(f"{path.name} not built")
+    return read_programs(path)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_programs_well_formed(n):
+    progs = _programs(n)
+    red = [g for g in o_enum(n) if tuple(g.key()) <= tuple(g.mirror().key())]
+    assert sorted(progs) == sorted(_name(g) for g in red)
+    for name, p in progs.items():
+        assert p["n_lines"] == 3 * n and p["n_lines"] <= p["n_regs"] <= 512 and len(p["kon"]) <= 512
+        ins = p["ins"]
+        op, a, b = ins & 15, (ins >> 4) & 1023, (ins >> 14) & 1023
+        assert (ins >> 24).max() == 0 and op.max() <= 10
+        end = int(np.argmax(op == 0))
+        assert op[end] == 0
+        ok = lambda x: np.where(x >= 512, x - 512 < len(p["kon"]), x < p["n_regs"])   # noqa: E731
+        for o in (1, 2, 3):
+            assert ok(a[:end][op[:end] == o]).all(), name
+        for o in (4, 5, 9, 10):
+            sel = op[:end] == o
+            assert ok(a[:end][sel]).all() and ok(b[:end][sel]).all(), name
+        st = a[:end][op[:end] == 8]
+        assert ((st >= p["n_lines"]) & (st < p["n_regs"])).all(), name
+
+
+@pytest.mark.parametrize("n,sel", [(2, None), (3, [0, 9, 19, 27])])
+def test_programs_match_oracle(n, sel):
+    progs = _programs(n)
+    red = [(i, g) for i, g in enumerate(o_enum(n)) if tuple(g.key()) <= tuple(g.mirror().key())]
+    if sel is not None:
+        red = [red[i] for i in sel]
+    rng = np.random.default_rng(7)
+    for i, g in red:
+        z = rng.random((6, g.n_lines)) ** 3 + 1e-3
+        z /= z.max(axis=1, keepdims=True)
+        fo = Integrand(g)(z, dtype=np.longdouble)
+        fv, W = interpret(progs[_name(g)], z, np.longdouble)
+        np.testing.assert_allclose(fv.astype(float), fo.astype(float), rtol=1e-12, atol=0, err_msg=_name(g))
+        # the absolute sum bounds the value
+        assert np.all(W >= np.abs(fv) * (1 - 1e-12))
+
+
+def test_four_loop_programs_match_stored_oracle():
+    progs = _programs(4)
+    if not GOLDEN4.exists():
+        pytest.skip("four_loop_points.txt not written")
+    rows = [ln.split() for ln in GOLDEN4.read_text().splitlines() if ln and not ln.startswith("#")]
+    gs = o_enum(4)
+    byg = {}
+    for r in rows:
+        byg.setdefault(int(r[0]), []).append(r)
+    assert len(byg) >= 4
+    for gi, rs in byg.items():
+        z = np.array([[float(v) for v in r[3:15]] for r in rs])
+        fo = np.array([np.longdouble(r[15]) for r in rs])
+        fv, W = interpret(progs[_name(gs[gi])], z, np.longdouble)
+        # both sides are long double in different operation orders: each is
+        # within a few ulp(long double) times the condition number
+        # kappa = (sum of |monomials|) / |f| that the program's W measures
+        kappa = (W / np.abs(fv)).astype(float)
+        rel = np.abs((fv - fo) / fo).astype(float)
+        assert np.all(rel <= 1e-12 + 16 * 2.0 ** -64 * kappa), (gi, rel, kappa)
