@@ -147,6 +147,7 @@ def load_library():
         "qed_diagram_calibrate_deg": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64]),
         "qed_diagram_get_deg": (C.c_int, [C.c_void_p, P(C.c_double)]),
         "qed_programs_load": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, P(C.c_int)]),
+        "qed_ctx_set_vm": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -232,6 +233,10 @@ class Context:
         _check(load_library().qed_programs_load(self._h, data, len(data), C.byref(cnt)))
         self.n_programs += cnt.value
         return cnt.value
+
+    def set_vm(self, threads: int = 128, points: int = 2):
+        """qed_ctx_set_vm: block size and points per thread of the interpreter kernels."""
+        _check(load_library().qed_ctx_set_vm(self._h, threads, points))
 
     def set_launch(self, threads: int, blocks: int = 0):
         _check(load_library().qed_ctx_set_launch(self._h, threads, blocks))

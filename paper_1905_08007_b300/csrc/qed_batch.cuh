@@ -22,7 +22,7 @@ struct BatchDiag {
   int N;
   int pad;
   // bytecode integrand (fid < 0): program, constants, their counts
-  const uint32_t *vins;
+  const uint2 *vins;
   const double *vkon;
   int vnk, vnr;
 };

@@ -1170,7 +1170,7 @@ static void gen_vm_order(const std::string &dir, int n, GenStats &st, const std:
   for (size_t i = 0; i < es.size(); ++i) {
     st.terms += sts[i].terms;
     st.monos += sts[i].monos;
-    ins += es[i].prog.ins.size();
+    ins += es[i].prog.code.size();
     flops += es[i].prog.flops;
     regs = std::max(regs, es[i].prog.n_regs);
   }

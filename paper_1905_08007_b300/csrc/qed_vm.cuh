@@ -23,12 +23,27 @@
 //   Constants live in shared memory (value and |value|).
 #pragma once
 #include "qed_kernels.cuh"
+#include "qed_batch.cuh"
 
-enum VmOp : uint32_t { VM_END = 0, VM_LD, VM_ADD, VM_MUL, VM_FMA, VM_FMAC, VM_RCP, VM_ABS, VM_ST, VM_ACCW, VM_LDMUL };
+// Instruction (64 bits, written by the generator's fuse step):
+//   lo = A | B << 10 | D << 20 | XA << 30 | ZO << 31,  hi = SPEC | NOCOMP << 3
+//   1. unless NOCOMP:  X = XA ? A : acc,  O = XA ? acc : A,
+//                      acc = X * B + (ZO ? O : 0)          (e lane alike)
+//   2. SPEC 1: acc = 1 / acc, e = |acc|;  2: e = |acc|;  3: W += |A.v| * B.e;
+//      4: end
+//   3. store acc in R[D] (D = 0: in the spare register)
+// Operands A, B: a register index, or 512 + a constant index.  Every
+// instruction reads both operands (the generator names the constants 0 or 1
+// where one is unused), so the common path has no branch on the operation.
 #define VM_KFLAG 512u
+#define VM_SP_RCP 1u
+#define VM_SP_ABS 2u
+#define VM_SP_ACCW 3u
+#define VM_SP_END 4u
+#define VM_NOCOMP 8u
 
 struct VmCode {
-  const uint32_t *ins;    // instruction words, END-padded to a multiple of 4
+  const uint2 *ins;       // instructions (lo, hi), END-padded to an even count
   const double *kon;      // constants
   int n_kon, n_regs;
 };
@@ -53,256 +68,353 @@ template <class E> __device__ __forceinline__ E vm_abs_e(double m);
 template <> __device__ __forceinline__ float vm_abs_e<float>(double m) { return float(m); }
 template <> __device__ __forceinline__ double vm_abs_e<double>(double m) { return m; }
 
-// Evaluate one program for this thread's point (already in R[0..N)).
-// kv/ke: constants and their magnitudes (shared memory); rv/re: this
-// thread's register file (shared memory, stride T).  Returns the integrand;
-// absum receives its monomial absolute sum (+inf when the FP32 lane lost
-// range, which flags the point).
-template <class R>
-__device__ __forceinline__ R vm_run(const uint32_t *__restrict__ ins, const double *__restrict__ kv,
-                                    const typename VmE<R>::T *__restrict__ ke, R *__restrict__ rv,
-                                    typename VmE<R>::T *__restrict__ re, int T, double &absum) {
-  typedef typename VmE<R>::T E;
-  R acc(0.0);
-  E ae = E(0);
-  double W = 0.0;
-  auto get = [&](uint32_t a, R &v, E &e) {
-    if (a >= VM_KFLAG) { v = R(kv[a - VM_KFLAG]); e = ke[a - VM_KFLAG]; }
-    else { v = rv[a * T]; e = re[a * T]; }
-  };
-  // the next group of four words is loaded while this one executes (the
-  // host leaves at least 16 readable bytes after every program)
-  const uint4 *p = reinterpret_cast<const uint4 *>(ins);
-  uint4 qn = __ldg(p);
-  for (;; ++p) {
-    const uint4 q = qn;
-    qn = __ldg(p + 1);
+// P consecutive values at a shared-memory byte offset (vector loads where
+// the layout makes them 8- or 16-byte aligned)
+template <class T, int P> struct VmVec {
+  __device__ static __forceinline__ void ld(const unsigned char *p, T (&v)[P]) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t w = j == 0 ? q.x : (j == 1 ? q.y : (j == 2 ? q.z : q.w));
-      const uint32_t op = w & 15u, a = (w >> 4) & 1023u, b = (w >> 14) & 1023u;
-      R va, vb;
-      E ea, eb;
-      switch (op) {
-        case VM_END:
-          absum = W;
-          return acc;
-        case VM_LD: get(a, acc, ae); break;
-        case VM_ADD: get(a, va, ea); acc = acc + va; ae = ae + ea; break;
-        case VM_MUL: get(a, va, ea); acc = acc * va; ae = ae * ea; break;
-        case VM_FMA: get(a, va, ea); get(b, vb, eb); acc = vm_fma(acc, va, vb); ae = ae * ea + eb; break;
-        case VM_FMAC: get(a, va, ea); get(b, vb, eb); acc = vm_fma(va, vb, acc); ae = ea * eb + ae; break;
-        case VM_RCP: acc = vm_rcp(acc); ae = vm_abs_e<E>(vm_mag(acc)); break;
-        case VM_ABS: ae = vm_abs_e<E>(vm_mag(acc)); break;
-        case VM_ST: rv[a * T] = acc; re[a * T] = ae; break;
-        case VM_ACCW:
-          get(a, va, ea); get(b, vb, eb);
-          // range guard of the FP32 lane: a block value whose absolute sum
-          // is (near) underflow or overflow cannot bound the rounding error
-          if (sizeof(E) == 4 && (!(double(eb) < 3.0e38) || (double(eb) < double(VM_E_FLOOR) && vm_mag(vb) != 0.0)))
-            W = __longlong_as_double(0x7ff0000000000000ll);
-          else
-            W = fma(vm_mag(va), double(eb), W);
-          break;
-        case VM_LDMUL: get(a, va, ea); get(b, vb, eb); acc = va * vb; ae = ea * eb; break;
-        default: break;
-      }
-    }
+    for (int i = 0; i < P; ++i) v[i] = reinterpret_cast<const T *>(p)[i];
   }
-}
+  __device__ static __forceinline__ void st(unsigned char *p, const T (&v)[P]) {
+#pragma unroll
+    for (int i = 0; i < P; ++i) reinterpret_cast<T *>(p)[i] = v[i];
+  }
+};
+template <> struct VmVec<double, 2> {
+  __device__ static __forceinline__ void ld(const unsigned char *p, double (&v)[2]) {
+    const double2 x = *reinterpret_cast<const double2 *>(p);
+    v[0] = x.x; v[1] = x.y;
+  }
+  __device__ static __forceinline__ void st(unsigned char *p, const double (&v)[2]) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+  }
+};
+template <> struct VmVec<float, 2> {
+  __device__ static __forceinline__ void ld(const unsigned char *p, float (&v)[2]) {
+    const float2 x = *reinterpret_cast<const float2 *>(p);
+    v[0] = x.x; v[1] = x.y;
+  }
+  __device__ static __forceinline__ void st(unsigned char *p, const float (&v)[2]) {
+    *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+  }
+};
 
-// Shared-memory layout of a VM kernel: constants (value, magnitude), then the
-// register files (value lanes, then e lanes).
-template <class R>
+// Shared-memory frame of a block: the constants (value and magnitude, each
+// repeated P times), then the register files, value lanes then e lanes, of
+// n_regs + 1 registers (the last takes the stores of instructions without a
+// target), register r of point p of thread t at ((r * T) + t) * P + p.
+template <class R, int P>
 __host__ __device__ __forceinline__ size_t vm_smem_bytes(int n_kon, int n_regs, int T) {
   typedef typename VmE<R>::T E;
-  const size_t k = (size_t(n_kon) * (sizeof(double) + sizeof(E)) + 15) & ~size_t(15);
-  return k + size_t(n_regs) * T * (sizeof(R) + sizeof(E));
+  const size_t k = (size_t(n_kon) * P * (sizeof(R) + sizeof(E)) + 15) & ~size_t(15);
+  return k + size_t(n_regs + 1) * T * P * (sizeof(R) + sizeof(E));
 }
 
-template <class R>
+template <class R, int P>
 struct VmFrame {
   typedef typename VmE<R>::T E;
-  const double *kv;
-  const E *ke;
-  R *rv;
-  E *re;
-  int T;
+  unsigned char *sm;
+  uint32_t kv, ke;          // byte offsets of the constant tables
+  uint32_t vt, et;          // this thread's register 0 (value, e lane)
+  uint32_t vs, es;          // bytes from one register to the next
+  uint32_t spare;
   __device__ __forceinline__ void setup(const VmCode &C, unsigned char *smem) {
-    double *k = reinterpret_cast<double *>(smem);
-    E *kabs = reinterpret_cast<E *>(smem + size_t(C.n_kon) * sizeof(double));
-    for (int i = threadIdx.x; i < C.n_kon; i += blockDim.x) {
-      const double c = C.kon[i];
-      k[i] = c;
+    sm = smem;
+    const int T = blockDim.x;
+    kv = 0;
+    ke = uint32_t(C.n_kon) * P * sizeof(R);
+    R *k = reinterpret_cast<R *>(smem);
+    E *kabs = reinterpret_cast<E *>(smem + ke);
+    for (int i = threadIdx.x; i < C.n_kon * P; i += blockDim.x) {
+      const double c = C.kon[i / P];
+      k[i] = R(c);
       kabs[i] = E(fabs(c));
     }
-    const size_t off = (size_t(C.n_kon) * (sizeof(double) + sizeof(E)) + 15) & ~size_t(15);
-    T = blockDim.x;
-    R *rbase = reinterpret_cast<R *>(smem + off);
-    E *ebase = reinterpret_cast<E *>(smem + off + size_t(C.n_regs) * T * sizeof(R));
-    kv = k;
-    ke = kabs;
-    rv = rbase + threadIdx.x;
-    re = ebase + threadIdx.x;
+    const uint32_t v0 = uint32_t((size_t(C.n_kon) * P * (sizeof(R) + sizeof(E)) + 15) & ~size_t(15));
+    const uint32_t e0 = v0 + uint32_t(C.n_regs + 1) * T * P * sizeof(R);
+    vs = uint32_t(T) * P * sizeof(R);
+    es = uint32_t(T) * P * sizeof(E);
+    vt = v0 + threadIdx.x * P * sizeof(R);
+    et = e0 + threadIdx.x * P * sizeof(E);
+    spare = uint32_t(C.n_regs);
     __syncthreads();
   }
-  template <int N>
-  __device__ __forceinline__ R eval(const VmCode &C, const R *z, double &absum) {
+  __device__ __forceinline__ void put(uint32_t r, const R (&v)[P], const E (&e)[P]) {
+    VmVec<R, P>::st(sm + vt + r * vs, v);
+    VmVec<E, P>::st(sm + et + r * es, e);
+  }
+  __device__ __forceinline__ void get(uint32_t a, R (&v)[P], E (&e)[P]) const {
+    const bool k = a >= VM_KFLAG;
+    const uint32_t i = a & (VM_KFLAG - 1u);
+    const uint32_t vo = k ? kv + i * uint32_t(P * sizeof(R)) : vt + a * vs;
+    const uint32_t eo = k ? ke + i * uint32_t(P * sizeof(E)) : et + a * es;
+    VmVec<R, P>::ld(sm + vo, v);
+    VmVec<E, P>::ld(sm + eo, e);
+  }
+
+  // One instruction whose operands are already loaded: compute, special,
+  // store.  Returns true at END.
+  __device__ __forceinline__ bool step(uint32_t lo, uint32_t hi, const R (&va)[P], const E (&ea)[P],
+                                       const R (&vb)[P], const E (&eb)[P], R (&acc)[P], E (&ae)[P],
+                                       double (&W)[P]) {
+    if (!(hi & VM_NOCOMP)) {
+      const bool xa = (lo >> 30) & 1u, zo = lo >> 31;
 #pragma unroll
-    for (int i = 0; i < N; ++i) { rv[i * T] = z[i]; re[i * T] = E(vm_mag(z[i])); }
-    return vm_run<R>(C.ins, kv, ke, rv, re, T, absum);
+      for (int p = 0; p < P; ++p) {
+        const R X = xa ? va[p] : acc[p], O = xa ? acc[p] : va[p];
+        const E eX = xa ? ea[p] : ae[p], eO = xa ? ae[p] : ea[p];
+        acc[p] = vm_fma(X, vb[p], zo ? O : R(0.0));
+        ae[p] = eX * eb[p] + (zo ? eO : E(0));
+      }
+    }
+    const uint32_t sp = hi & 7u;
+    if (sp) {
+      if (sp == VM_SP_END) return true;
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        if (sp == VM_SP_RCP) { acc[p] = vm_rcp(acc[p]); ae[p] = vm_abs_e<E>(vm_mag(acc[p])); }
+        else if (sp == VM_SP_ABS) ae[p] = vm_abs_e<E>(vm_mag(acc[p]));
+        else if (sp == VM_SP_ACCW) {
+          // range guard of the FP32 lane: a block value whose absolute sum
+          // is (near) underflow or overflow cannot bound the error
+          if (sizeof(E) == 4 && (!(double(eb[p]) < 3.0e38) ||
+                                 (double(eb[p]) < double(VM_E_FLOOR) && vm_mag(vb[p]) != 0.0)))
+            W[p] = __longlong_as_double(0x7ff0000000000000ll);
+          else
+            W[p] = fma(vm_mag(va[p]), double(eb[p]), W[p]);
+        }
+      }
+    }
+    const uint32_t d = (lo >> 20) & 1023u;
+    put(d ? d : spare, acc, ae);
+    return false;
+  }
+
+  // Evaluate the program at the P points z[p][0..N): returns f[p] and the
+  // monomial absolute sums absum[p] (+inf where the FP32 lane lost range,
+  // which flags the point).  Software pipelined: the operands of the next
+  // instruction are loaded before this one computes and stores (the
+  // generator never lets an instruction read the register the previous one
+  // writes), so shared-memory latency is off the chain through acc; the
+  // instruction stream is loaded four 16-byte groups (eight instructions)
+  // ahead.  The host pads every program with zero words to an even count
+  // plus four zero groups, so every look-ahead stays inside the program.
+  template <int N>
+  __device__ __forceinline__ void eval(const VmCode &C, const R (&z)[P][N], R (&f)[P], double (&absum)[P]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      R v[P];
+      E e[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) { v[p] = z[p][i]; e[p] = E(vm_mag(z[p][i])); }
+      put(uint32_t(i), v, e);
+    }
+    R acc[P];
+    E ae[P];
+    double W[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) { acc[p] = R(0.0); ae[p] = E(0); W[p] = 0.0; }
+    const uint4 *ip = reinterpret_cast<const uint4 *>(C.ins);
+    uint4 g0 = __ldg(ip), g1 = __ldg(ip + 1), g2 = __ldg(ip + 2), g3 = __ldg(ip + 3);
+    R va[P], vb[P], na[P], nb[P];
+    E ea[P], eb[P], nea[P], neb[P];
+    get(g0.x & 1023u, va, ea);
+    get((g0.x >> 10) & 1023u, vb, eb);
+    for (;; ++ip) {
+      get(g0.z & 1023u, na, nea);
+      get((g0.z >> 10) & 1023u, nb, neb);
+      if (step(g0.x, g0.y, va, ea, vb, eb, acc, ae, W)) break;
+      get(g1.x & 1023u, va, ea);
+      get((g1.x >> 10) & 1023u, vb, eb);
+      if (step(g0.z, g0.w, na, nea, nb, neb, acc, ae, W)) break;
+      g0 = g1;
+      g1 = g2;
+      g2 = g3;
+      g3 = __ldg(ip + 4);
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) { f[p] = acc[p]; absum[p] = W[p]; }
   }
 };
 
 // ---------------------------------------------------------------------------
 // kernels (the Eq. (1) tables are read from global memory: at N = 12 they
-// are 96 KB, and shared memory holds the register files)
+// are 96 KB, and shared memory holds the register files).  The FP64 kernels
+// evaluate P points per thread with one instruction stream: sample i and
+// i + (threads in the grid) for the per-graph kernels, offset o and
+// o + blockDim for the batched one.  A point past the end of the range
+// repeats the first one and is discarded.
 // ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(256) k_integrate_vm(KParams P, VmCode C) {
+template <int N, int P>
+__global__ void __launch_bounds__(256) k_integrate_vm(KParams K, VmCode C) {
   extern __shared__ __align__(16) unsigned char vsm[];
-  VmFrame<double> fr;
+  VmFrame<double, P> fr;
   fr.setup(C, vsm);
   KSum sw, sw2;
   unsigned long long nflag = 0;
-  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P.n; i += stride) {
-    const uint64_t s = P.begin + i;
-    double z[N];
-    const double lp = draw_point<N>(s, P, P.F, P.G, P.invdeg, z);
-    double absum;
-    const double f = fr.eval<N>(C, z, absum);
-    const double w = f * exp(-lp);
-    const bool bad = !isfinite(w) || !(rel_err_estimate(f, absum, 1.1102230246251565e-16) <= P.thresh);
-    if (bad) {
-      ++nflag;
-      const unsigned int slot = atomicAdd(P.queue_len, 1u);
-      if (slot < P.queue_cap) P.queue[slot] = i;
-    } else {
-      sw.add(w);
-      sw2.add(w * w);
+  const uint64_t nth = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < K.n; i0 += nth * P) {
+    double z[P][N], lp[P], f[P], ab[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const uint64_t i = i0 + p * nth;
+      lp[p] = draw_point<N>(K.begin + (i < K.n ? i : i0), K, K.F, K.G, K.invdeg, z[p]);
+    }
+    fr.template eval<N>(C, z, f, ab);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const uint64_t i = i0 + p * nth;
+      if (i >= K.n) continue;
+      const double w = f[p] * exp(-lp[p]);
+      if (!isfinite(w) || !(rel_err_estimate(f[p], ab[p], 1.1102230246251565e-16) <= K.thresh)) {
+        ++nflag;
+        const unsigned int slot = atomicAdd(K.queue_len, 1u);
+        if (slot < K.queue_cap) K.queue[slot] = i;
+      } else {
+        sw.add(w);
+        sw2.add(w * w);
+      }
     }
   }
-  block_reduce_store(sw, sw2, nflag, 0ull, P.partials, P.counts, blockIdx.x);
+  block_reduce_store(sw, sw2, nflag, 0ull, K.partials, K.counts, blockIdx.x);
 }
 
-// Double-double re-evaluation of the queued samples (offsets from P.begin).
-// A queue overflow is handled on the host by re-collecting the flagged
-// offsets of sub-ranges no longer than the queue.
+// Double-double re-evaluation of the queued samples (offsets from K.begin).
 template <int N>
-__global__ void __launch_bounds__(256) k_redo_dd_vm(KParams P, VmCode C, unsigned int qn) {
+__global__ void __launch_bounds__(256) k_redo_dd_vm(KParams K, VmCode C, unsigned int qn) {
   extern __shared__ __align__(16) unsigned char vsm[];
-  VmFrame<dd> fr;
+  VmFrame<dd, 1> fr;
   fr.setup(C, vsm);
   KSum sw, sw2;
   unsigned long long nunst = 0;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < qn; i += stride) {
     double z[N];
-    const double lp = draw_point<N>(P.begin + P.queue[i], P, P.F, P.G, P.invdeg, z);
-    dd zd[N];
+    const double lp = draw_point<N>(K.begin + K.queue[i], K, K.F, K.G, K.invdeg, z);
+    dd zd[1][N], f[1];
+    double ab[1];
 #pragma unroll
-    for (int L = 0; L < N; ++L) zd[L] = dd{z[L], 0.0};
-    double absum;
-    const dd f = fr.eval<N>(C, zd, absum);
-    const double w = (f.hi + f.lo) * exp(-lp);
-    if (!isfinite(w) || !(rel_err_estimate(f.hi, absum, 1.2325951644078309e-32) <= P.thresh)) {
+    for (int L = 0; L < N; ++L) zd[0][L] = dd{z[L], 0.0};
+    fr.template eval<N>(C, zd, f, ab);
+    const double w = (f[0].hi + f[0].lo) * exp(-lp);
+    if (!isfinite(w) || !(rel_err_estimate(f[0].hi, ab[0], 1.2325951644078309e-32) <= K.thresh)) {
       ++nunst;
       continue;
     }
     sw.add(w);
     sw2.add(w * w);
   }
-  block_reduce_store(sw, sw2, 0ull, nunst, P.partials, P.counts, blockIdx.x);
+  block_reduce_store(sw, sw2, 0ull, nunst, K.partials, K.counts, blockIdx.x);
 }
 
-template <int N>
-__global__ void __launch_bounds__(256) k_dump_vm(KParams P, VmCode C) {
+template <int N, int P>
+__global__ void __launch_bounds__(256) k_dump_vm(KParams K, VmCode C) {
   extern __shared__ __align__(16) unsigned char vsm[];
-  VmFrame<double> fr;
+  VmFrame<double, P> fr;
   fr.setup(C, vsm);
-  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P.n; i += stride) {
-    double z[N];
-    const double lp = draw_point<N>(P.begin + i, P, P.F, P.G, P.invdeg, z);
-    double absum;
-    const double f = fr.eval<N>(C, z, absum);
-    const double w = f * exp(-lp);
-    uint8_t flag = 0;
-    if (!(rel_err_estimate(f, absum, 1.1102230246251565e-16) <= P.thresh)) flag |= 1;
-    if (!isfinite(w)) flag |= 2;
+  const uint64_t nth = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < K.n; i0 += nth * P) {
+    double z[P][N], lp[P], f[P], ab[P];
 #pragma unroll
-    for (int L = 0; L < N; ++L) P.z_out[i * N + L] = z[L];
-    P.f_out[i] = f;
-    P.lp_out[i] = lp;
-    P.flag_out[i] = flag;
+    for (int p = 0; p < P; ++p) {
+      const uint64_t i = i0 + p * nth;
+      lp[p] = draw_point<N>(K.begin + (i < K.n ? i : i0), K, K.F, K.G, K.invdeg, z[p]);
+    }
+    fr.template eval<N>(C, z, f, ab);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const uint64_t i = i0 + p * nth;
+      if (i >= K.n) continue;
+      const double w = f[p] * exp(-lp[p]);
+      uint8_t flag = 0;
+      if (!(rel_err_estimate(f[p], ab[p], 1.1102230246251565e-16) <= K.thresh)) flag |= 1;
+      if (!isfinite(w)) flag |= 2;
+#pragma unroll
+      for (int L = 0; L < N; ++L) K.z_out[i * N + L] = z[p][L];
+      K.f_out[i] = f[p];
+      K.lp_out[i] = lp[p];
+      K.flag_out[i] = flag;
+    }
   }
 }
 
-// prec 0: FP64 (smem frame of doubles), prec 1: double-double
-template <int N>
+// prec 0: FP64 with P points per thread; prec 1: double-double, one point
+template <int N, int P>
 __global__ void __launch_bounds__(256) k_eval_vm(const double *__restrict__ zin, uint64_t n, int prec,
                                                  double *__restrict__ fout, VmCode C) {
   extern __shared__ __align__(16) unsigned char vsm[];
-  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  const uint64_t nth = uint64_t(gridDim.x) * blockDim.x;
   if (prec == 0) {
-    VmFrame<double> fr;
+    VmFrame<double, P> fr;
     fr.setup(C, vsm);
-    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
-      double z[N];
+    for (uint64_t i0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < n; i0 += nth * P) {
+      double z[P][N], f[P], ab[P];
 #pragma unroll
-      for (int L = 0; L < N; ++L) z[L] = zin[i * N + L];
-      double absum;
-      fout[i] = fr.eval<N>(C, z, absum);
+      for (int p = 0; p < P; ++p) {
+        const uint64_t i = i0 + p * nth, src = i < n ? i : i0;
+#pragma unroll
+        for (int L = 0; L < N; ++L) z[p][L] = zin[src * N + L];
+      }
+      fr.template eval<N>(C, z, f, ab);
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+        if (i0 + p * nth < n) fout[i0 + p * nth] = f[p];
     }
   } else {
-    VmFrame<dd> fr;
+    VmFrame<dd, 1> fr;
     fr.setup(C, vsm);
-    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
-      dd z[N];
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += nth) {
+      dd z[1][N], f[1];
+      double ab[1];
 #pragma unroll
-      for (int L = 0; L < N; ++L) z[L] = dd{zin[i * N + L], 0.0};
-      double absum;
-      const dd f = fr.eval<N>(C, z, absum);
-      fout[i] = f.hi + f.lo;
+      for (int L = 0; L < N; ++L) z[0][L] = dd{zin[i * N + L], 0.0};
+      fr.template eval<N>(C, z, f, ab);
+      fout[i] = f[0].hi + f[0].lo;
     }
   }
 }
 
 // Adjoint of the second moment over recomputed samples (same sums as
 // k_pdf_grad; the integrand is the program).  out: [gridDim.x][2N + 1].
-template <int N>
-__global__ void __launch_bounds__(256) k_pdf_grad_vm(KParams P, VmCode C, const uint8_t *__restrict__ act, double *out) {
+template <int N, int P>
+__global__ void __launch_bounds__(256) k_pdf_grad_vm(KParams K, VmCode C, const uint8_t *__restrict__ act, double *out) {
   extern __shared__ __align__(16) unsigned char vsm[];
-  VmFrame<double> fr;
+  VmFrame<double, P> fr;
   fr.setup(C, vsm);
   double m2 = 0.0, ga[N], gb[N];
 #pragma unroll
   for (int m = 0; m < N; ++m) { ga[m] = 0.0; gb[m] = 0.0; }
-  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P.n; i += stride) {
-    double z[N], lt[N];
-    int order[N];
-    const double lp = draw_point<N, true>(P.begin + i, P, P.F, P.G, P.invdeg, z, order, lt);
-    double absum;
-    const double f = fr.eval<N>(C, z, absum);
-    double w = f * exp(-lp);
-    if (!isfinite(w)) w = 0.0;
-    const double w2 = w * w;
-    m2 += w2;
-    double cum = 0.0;
-    uint32_t S = (1u << N) - 1u;
+  const uint64_t nth = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < K.n; i0 += nth * P) {
+    double z[P][N], lt[P][N], lp[P], f[P], ab[P];
+    int order[P][N];
 #pragma unroll
-    for (int r = 0; r < N; ++r) {
-      if (r > 0) {
-        S &= ~(1u << order[r - 1]);
-        if (act[S]) cum += lt[r];
+    for (int p = 0; p < P; ++p) {
+      const uint64_t i = i0 + p * nth;
+      lp[p] = draw_point<N, true>(K.begin + (i < K.n ? i : i0), K, K.F, K.G, K.invdeg, z[p], order[p], lt[p]);
+    }
+    fr.template eval<N>(C, z, f, ab);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      if (i0 + p * nth >= K.n) continue;
+      double w = f[p] * exp(-lp[p]);
+      if (!isfinite(w)) w = 0.0;
+      const double w2 = w * w;
+      m2 += w2;
+      double cum = 0.0;
+      uint32_t S = (1u << N) - 1u;
+#pragma unroll
+      for (int r = 0; r < N; ++r) {
+        if (r > 0) {
+          S &= ~(1u << order[p][r - 1]);
+          if (act[S]) cum += lt[p][r];
+        }
+#pragma unroll
+        for (int m = 0; m < N; ++m) if (order[p][r] == m) ga[m] += w2 * cum;
       }
 #pragma unroll
-      for (int m = 0; m < N; ++m) if (order[r] == m) ga[m] += w2 * cum;
+      for (int m = 0; m < N; ++m) if (order[p][0] == m) gb[m] += w2;
     }
-#pragma unroll
-    for (int m = 0; m < N; ++m) if (order[0] == m) gb[m] += w2;
   }
   __shared__ double red[8][2 * N + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -328,8 +440,9 @@ __global__ void __launch_bounds__(256) k_pdf_grad_vm(KParams P, VmCode C, const 
 // batched integration of a set of bytecode graphs (one line count N): the
 // same scheduler as k_batch_fp64 / k_batch_dd.  The flagged list of an item
 // holds a whole chunk, so it never overflows and the dd pass needs no rescan.
+// The list order is the order of the offsets, whatever P is.
 // ---------------------------------------------------------------------------
-template <int N>
+template <int N, int P>
 __global__ void __launch_bounds__(256) k_batch_vm_fp64(BatchParams B) {
   extern __shared__ __align__(16) unsigned char vsm[];
   __shared__ unsigned int s_item;
@@ -344,37 +457,44 @@ __global__ void __launch_bounds__(256) k_batch_vm_fp64(BatchParams B) {
     if (it >= B.n_items) break;
     const BatchItem I = B.items[it];
     const BatchDiag &D = B.diags[I.diag];
-    const KParams P = batch_kparams(B, D);
+    const KParams K = batch_kparams(B, D);
     const VmCode C = {D.vins, D.vkon, D.vnk, D.vnr};
-    VmFrame<double> fr;
+    VmFrame<double, P> fr;
     fr.setup(C, vsm);
     if (threadIdx.x == 0) s_base = 0;
     __syncthreads();
     KSum sw, sw2;
-    for (uint32_t off0 = 0; off0 < I.count; off0 += blockDim.x) {
-      const uint32_t off = off0 + threadIdx.x;
-      bool flagged = false;
-      if (off < I.count) {
-        double z[N];
-        const double lp = draw_point<N>(I.begin + off, P, P.F, P.G, P.invdeg, z);
-        double absum;
-        const double f = fr.eval<N>(C, z, absum);
-        const double w = f * exp(-lp);
-        if (!isfinite(w) || !(rel_err_estimate(f, absum, 1.1102230246251565e-16) <= P.thresh)) flagged = true;
-        else { sw.add(w); sw2.add(w * w); }
+    for (uint32_t off0 = 0; off0 < I.count; off0 += blockDim.x * P) {
+      double z[P][N], lp[P], f[P], ab[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const uint32_t off = off0 + p * blockDim.x + threadIdx.x;
+        lp[p] = draw_point<N>(I.begin + (off < I.count ? off : off0 + threadIdx.x < I.count ? off0 + threadIdx.x : 0),
+                              K, K.F, K.G, K.invdeg, z[p]);
       }
-      const unsigned int m = __ballot_sync(0xffffffffu, flagged);
-      if (lane == 0) wcount[warp] = __popc(m);
-      __syncthreads();
-      unsigned int before = s_base, total = 0;
-      for (int w = 0; w < nwarp; ++w) { if (w < warp) before += wcount[w]; total += wcount[w]; }
-      if (flagged) {
-        const unsigned int pos = before + __popc(m & ((1u << lane) - 1u));
-        if (pos < B.list_cap) B.lists[size_t(it) * B.list_cap + pos] = off;
+      fr.template eval<N>(C, z, f, ab);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const uint32_t off = off0 + p * blockDim.x + threadIdx.x;
+        bool flagged = false;
+        if (off < I.count) {
+          const double w = f[p] * exp(-lp[p]);
+          if (!isfinite(w) || !(rel_err_estimate(f[p], ab[p], 1.1102230246251565e-16) <= K.thresh)) flagged = true;
+          else { sw.add(w); sw2.add(w * w); }
+        }
+        const unsigned int m = __ballot_sync(0xffffffffu, flagged);
+        if (lane == 0) wcount[warp] = __popc(m);
+        __syncthreads();
+        unsigned int before = s_base, total = 0;
+        for (int w = 0; w < nwarp; ++w) { if (w < warp) before += wcount[w]; total += wcount[w]; }
+        if (flagged) {
+          const unsigned int pos = before + __popc(m & ((1u << lane) - 1u));
+          if (pos < B.list_cap) B.lists[size_t(it) * B.list_cap + pos] = off;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_base += total;
+        __syncthreads();
       }
-      __syncthreads();
-      if (threadIdx.x == 0) s_base += total;
-      __syncthreads();
     }
     block_reduce_store(sw, sw2, threadIdx.x == 0 ? (unsigned long long)s_base : 0ull, 0ull, B.part, B.cnt, it);
     __syncthreads();
@@ -397,9 +517,9 @@ __global__ void __launch_bounds__(256) k_batch_vm_dd(BatchParams B) {
       continue;
     }
     const BatchDiag &D = B.diags[I.diag];
-    const KParams P = batch_kparams(B, D);
+    const KParams K = batch_kparams(B, D);
     const VmCode C = {D.vins, D.vkon, D.vnk, D.vnr};
-    VmFrame<dd> fr;
+    VmFrame<dd, 1> fr;
     fr.setup(C, vsm);
     const uint64_t total = nflag < B.list_cap ? nflag : B.list_cap;
     KSum sw, sw2;
@@ -407,14 +527,14 @@ __global__ void __launch_bounds__(256) k_batch_vm_dd(BatchParams B) {
     for (uint64_t i = threadIdx.x; i < total; i += blockDim.x) {
       const uint32_t off = B.lists[size_t(it) * B.list_cap + i];
       double z[N];
-      const double lp = draw_point<N>(I.begin + off, P, P.F, P.G, P.invdeg, z);
-      dd zd[N];
+      const double lp = draw_point<N>(I.begin + off, K, K.F, K.G, K.invdeg, z);
+      dd zd[1][N], f[1];
+      double ab[1];
 #pragma unroll
-      for (int L = 0; L < N; ++L) zd[L] = dd{z[L], 0.0};
-      double absum;
-      const dd f = fr.eval<N>(C, zd, absum);
-      const double w = (f.hi + f.lo) * exp(-lp);
-      if (!isfinite(w) || !(rel_err_estimate(f.hi, absum, 1.2325951644078309e-32) <= P.thresh)) { ++nunst; continue; }
+      for (int L = 0; L < N; ++L) zd[0][L] = dd{z[L], 0.0};
+      fr.template eval<N>(C, zd, f, ab);
+      const double w = (f[0].hi + f[0].lo) * exp(-lp);
+      if (!isfinite(w) || !(rel_err_estimate(f[0].hi, ab[0], 1.2325951644078309e-32) <= K.thresh)) { ++nunst; continue; }
       sw.add(w);
       sw2.add(w * w);
     }
@@ -423,11 +543,12 @@ __global__ void __launch_bounds__(256) k_batch_vm_dd(BatchParams B) {
   }
 }
 
-// Kernel table of the bytecode path for one line count.
+// Kernel table of the bytecode path for one line count N and P points per
+// thread in the FP64 kernels.
 struct VmKernelSet {
   const void *integrate, *redo, *dump, *eval, *grad, *batch64, *batchdd;
 };
-#define QED_VM_KSET(N)                                                                                       \
-  VmKernelSet{(const void *)k_integrate_vm<N>, (const void *)k_redo_dd_vm<N>, (const void *)k_dump_vm<N>,   \
-              (const void *)k_eval_vm<N>, (const void *)k_pdf_grad_vm<N>, (const void *)k_batch_vm_fp64<N>, \
-              (const void *)k_batch_vm_dd<N>}
+#define QED_VM_KSET(N, P)                                                                                       \
+  VmKernelSet{(const void *)k_integrate_vm<N, P>, (const void *)k_redo_dd_vm<N>, (const void *)k_dump_vm<N, P>, \
+              (const void *)k_eval_vm<N, P>, (const void *)k_pdf_grad_vm<N, P>,                                 \
+              (const void *)k_batch_vm_fp64<N, P>, (const void *)k_batch_vm_dd<N>}

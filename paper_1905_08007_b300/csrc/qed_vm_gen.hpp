@@ -23,8 +23,7 @@
 //   path accumulates; W receives |prefactor| * e(block value) per forest term
 //   in double, as the compiled path does.
 //
-// Instruction word (32 bits): op[0:4) a[4:14) b[14:24); operands are a
-// register index, or 512 + a constant index.
+// The code generator works on micro-operations:
 //   END                          v, W are the integrand and its absolute sum
 //   LD a        acc = a
 //   ADD a       acc = acc + a
@@ -36,6 +35,23 @@
 //   ST a        R[a] = acc
 //   ACCW a b    W += |a.v| * b.e
 //   LDMUL a b   acc = a * b
+// (operands: a register index, or 512 + a constant index), and fuses them
+// into 64-bit instructions that the interpreter executes without a dispatch
+// on the operation:
+//   lo = A | B << 10 | D << 20 | XA << 30 | ZO << 31,  hi = SPEC | NOCOMP << 3
+//   1. unless NOCOMP:  X = XA ? A : acc,  O = XA ? acc : A,
+//                      acc = X * B + (ZO ? O : 0)           (e lane alike)
+//   2. SPEC 1 RCP: acc = 1 / acc, e = |acc|;  2 ABS: e = |acc|;
+//      3 ACCW: W += |A.v| * B.e;  4 END
+//   3. D != 0: R[D] = acc                     (register 0 is z[0], never stored)
+// LD a = (XA, A = a, B = 1); ADD a = (A = a, B = 1, ZO); MUL a = (B = a);
+// FMA a b = (A = b, B = a, ZO); FMAC a b = (XA, A = a, B = b, ZO);
+// LDMUL a b = (XA, A = a, B = b).  Each value is bit-identical to the
+// micro-operation's (x * 1 + 0 and x * y + 0 round like x and x * y).
+// The interpreter reads an instruction's operands before the previous
+// instruction stores, so no instruction reads the register the one before
+// it writes: where that would happen a no-operation (NOCOMP, constant
+// operands, no store) is put between them.
 #pragma once
 #include <cstdint>
 #include <cstdio>
@@ -56,6 +72,16 @@ constexpr int MAX_KON = 512;
 
 inline uint32_t enc(Op op, int a = 0, int b = 0) {
   return uint32_t(op) | (uint32_t(a) << 4) | (uint32_t(b) << 14);
+}
+
+enum : uint32_t { SP_NONE = 0, SP_RCP = 1, SP_ABS = 2, SP_ACCW = 3, SP_END = 4 };
+constexpr uint32_t NOCOMP = 8u;
+
+inline uint64_t word(int A, int B, int D, bool xa, bool zo, uint32_t spec, bool nocomp) {
+  const uint32_t lo = uint32_t(A) | (uint32_t(B) << 10) | (uint32_t(D) << 20) | (uint32_t(xa) << 30) |
+                      (uint32_t(zo) << 31);
+  const uint32_t hi = spec | (nocomp ? NOCOMP : 0u);
+  return uint64_t(lo) | (uint64_t(hi) << 32);
 }
 
 // ---------------------------------------------------------------------------
@@ -166,7 +192,8 @@ struct Stmt {
 };
 
 struct Program {
-  std::vector<uint32_t> ins;
+  std::vector<uint32_t> ins;      // micro-operations
+  std::vector<uint64_t> code;     // fused instructions (what the file holds)
   std::vector<double> kon;
   int n_regs = 0;
   double flops = 0.0;
@@ -264,6 +291,7 @@ class Compiler {
       }
     }
     P.n_regs = hi;
+    fuse();
     return P;
   }
 
@@ -362,6 +390,59 @@ class Compiler {
     free_reg(it->second);
     reg.erase(it);
   }
+  // micro-operations -> fused instructions: a compute step, then an optional
+  // special (RCP / ABS), then an optional store, share one instruction
+  void fuse() {
+    const int one = kon(1.0), zero = kon(0.0);
+    auto &C = P.code;
+    C.clear();
+    bool open = false;          // last instruction can still take a special / store
+    bool has_spec = false, has_st = false;
+    for (uint32_t w : P.ins) {
+      const int op = int(w & 15u), a = int((w >> 4) & 1023u), b = int((w >> 14) & 1023u);
+      auto put = [&](uint64_t x, bool can_extend) {
+        C.push_back(x);
+        open = can_extend;
+        has_spec = false;
+        has_st = false;
+      };
+      switch (op) {
+        case LD: put(word(a, one, 0, true, false, SP_NONE, false), true); break;
+        case ADD: put(word(a, one, 0, false, true, SP_NONE, false), true); break;
+        case MUL: put(word(zero, a, 0, false, false, SP_NONE, false), true); break;
+        case FMA: put(word(b, a, 0, false, true, SP_NONE, false), true); break;
+        case FMAC: put(word(a, b, 0, true, true, SP_NONE, false), true); break;
+        case LDMUL: put(word(a, b, 0, true, false, SP_NONE, false), true); break;
+        case RCP:
+        case ABS: {
+          const uint32_t sp = op == RCP ? SP_RCP : SP_ABS;
+          if (open && !has_spec && !has_st) { C.back() |= uint64_t(sp) << 32; has_spec = true; }
+          else { put(word(zero, one, 0, false, false, sp, true), true); has_spec = true; }
+          break;
+        }
+        case ST:
+          if (open && !has_st) { C.back() |= uint64_t(uint32_t(a) << 20); has_st = true; }
+          else { put(word(zero, one, a, false, false, SP_NONE, true), false); }
+          break;
+        case ACCW: put(word(a, b, 0, false, false, SP_ACCW, true), false); break;
+        case END: put(word(zero, one, 0, false, false, SP_END, true), false); break;
+        default: fprintf(stderr, "vm: bad micro-operation\n"); exit(1);
+      }
+    }
+    // separate read-after-write neighbours
+    std::vector<uint64_t> out;
+    out.reserve(C.size() + C.size() / 8);
+    for (size_t i = 0; i < C.size(); ++i) {
+      if (i > 0) {
+        const uint32_t d = uint32_t(C[i - 1] >> 20) & 1023u;
+        const uint32_t a = uint32_t(C[i]) & 1023u, b = uint32_t(C[i] >> 10) & 1023u;
+        if (d != 0 && (a == d || b == d)) out.push_back(word(zero, one, 0, false, false, SP_NONE, true));
+      }
+      out.push_back(C[i]);
+    }
+    C.swap(out);
+  }
+
   int kon(double c) {
     auto it = kidx.find(c);
     if (it != kidx.end()) return KFLAG + it->second;
@@ -503,9 +584,9 @@ class Compiler {
 // ---------------------------------------------------------------------------
 // program file
 // ---------------------------------------------------------------------------
-// Layout (little endian): "QEDVM001", u32 count, u32 0, then per program a
-// 64-byte name, i32 n_lines, n_regs, n_ins, n_kon, f64 flops, the
-// instruction words (padded to 8 bytes) and the constants.
+// Layout (little endian): "QEDVM002", u32 count, u32 0, then per program a
+// 64-byte name, i32 n_lines, n_regs, n_ins, n_kon, f64 flops, the n_ins
+// 64-bit instructions and the constants.
 struct Entry {
   std::string name;
   int n_lines;
@@ -515,18 +596,17 @@ struct Entry {
 inline void write_programs(const std::string &path, const std::vector<Entry> &es) {
   FILE *f = fopen(path.c_str(), "wb");
   if (!f) { fprintf(stderr, "vm: cannot write %s\n", path.c_str()); exit(1); }
-  fwrite("QEDVM001", 1, 8, f);
+  fwrite("QEDVM002", 1, 8, f);
   const uint32_t hdr[2] = {uint32_t(es.size()), 0u};
   fwrite(hdr, 4, 2, f);
   for (auto &e : es) {
     char nm[64] = {0};
     strncpy(nm, e.name.c_str(), 63);
     fwrite(nm, 1, 64, f);
-    const int32_t m[4] = {e.n_lines, e.prog.n_regs, int32_t(e.prog.ins.size()), int32_t(e.prog.kon.size())};
+    const int32_t m[4] = {e.n_lines, e.prog.n_regs, int32_t(e.prog.code.size()), int32_t(e.prog.kon.size())};
     fwrite(m, 4, 4, f);
     fwrite(&e.prog.flops, 8, 1, f);
-    fwrite(e.prog.ins.data(), 4, e.prog.ins.size(), f);
-    if (e.prog.ins.size() % 2) { const uint32_t z = 0; fwrite(&z, 4, 1, f); }
+    fwrite(e.prog.code.data(), 8, e.prog.code.size(), f);
     fwrite(e.prog.kon.data(), 8, e.prog.kon.size(), f);
   }
   fclose(f);

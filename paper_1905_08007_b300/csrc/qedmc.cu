@@ -52,9 +52,11 @@ QED_GENERATED_LIST(QED_DECL_KSET)
 static const KernelSet *const g_kernels[] = {QED_GENERATED_LIST(QED_REF_KSET)};
 // persistent batched kernels (defined in the generated batch translation unit)
 extern const void *const qed_batch_kernels[2];
-// bytecode path: one kernel set per line count N = 3n
-static const VmKernelSet g_vm_kernels[QED_MAX_LOOPS] = {QED_VM_KSET(3), QED_VM_KSET(6), QED_VM_KSET(9),
-                                                        QED_VM_KSET(12), QED_VM_KSET(15)};
+// bytecode path: one kernel set per line count N = 3n and points per thread
+// P of the FP64 kernels (1 or 2)
+static const VmKernelSet g_vm_kernels[2][QED_MAX_LOOPS] = {
+    {QED_VM_KSET(3, 1), QED_VM_KSET(6, 1), QED_VM_KSET(9, 1), QED_VM_KSET(12, 1), QED_VM_KSET(15, 1)},
+    {QED_VM_KSET(3, 2), QED_VM_KSET(6, 2), QED_VM_KSET(9, 2), QED_VM_KSET(12, 2), QED_VM_KSET(15, 2)}};
 
 // ---------------------------------------------------------------------------
 // host objects
@@ -81,13 +83,14 @@ struct qed_ctx {
     std::string name;
     int n_lines, n_regs, n_ins, n_kon;
     double flops;
-    const uint32_t *d_ins;
+    const uint2 *d_ins;
     const double *d_kon;
   };
   std::vector<VmProg> vm;
   std::vector<void *> vm_bufs;
   bool prefer_vm = false;
   int vm_threads = 128;      // threads per block of the FP64 interpreter kernels
+  int vm_points = 2;         // points per thread of the FP64 interpreter kernels
 };
 
 struct qed_diag {
@@ -222,6 +225,15 @@ extern "C" int qed_ctx_set_launch(qed_ctx *c, int threads, int blocks) {
   return QED_OK;
 }
 
+extern "C" int qed_ctx_set_vm(qed_ctx *c, int threads, int points) {
+  if (!c) return set_err(QED_EINVAL, "ctx is NULL");
+  if (threads < 32 || threads > 256 || threads % 32) return set_err(QED_EINVAL, "threads per block must be a multiple of 32 in [32, 256]");
+  if (points != 1 && points != 2) return set_err(QED_EINVAL, "points per thread must be 1 or 2");
+  c->vm_threads = threads;
+  c->vm_points = points;
+  return QED_OK;
+}
+
 extern "C" int qed_ctx_set_threshold(qed_ctx *c, double rel) {
   if (!c || !(rel > 0.0)) return set_err(QED_EINVAL, "threshold must be > 0");
   c->thresh = rel;
@@ -234,36 +246,39 @@ extern "C" int qed_ctx_set_threshold(qed_ctx *c, double rel) {
 // Every instruction is checked against its program's register and constant
 // counts here, so that the interpreter's shared-memory accesses stay inside
 // the frame the host sized for it.
-static bool vm_check(const uint32_t *ins, int n_ins, int n_regs, int n_kon, int n_lines, std::string &why) {
-  if (n_regs < n_lines || n_regs > 512 || n_kon < 0 || n_kon > 512 || n_ins < 1) { why = "program sizes out of range"; return false; }
+static bool vm_check(const uint2 *ins, int n_ins, int n_regs, int n_kon, int n_lines, std::string &why) {
+  if (n_regs < n_lines || n_regs > 511 || n_kon < 0 || n_kon > 512 || n_ins < 1) { why = "program sizes out of range"; return false; }
   auto ok = [&](uint32_t a) { return a < VM_KFLAG ? int(a) < n_regs : int(a - VM_KFLAG) < n_kon; };
-  bool ended = false;
   for (int i = 0; i < n_ins; ++i) {
-    const uint32_t w = ins[i], op = w & 15u, a = (w >> 4) & 1023u, b = (w >> 14) & 1023u;
-    if (w >> 24) { why = "reserved instruction bits set"; return false; }
-    switch (op) {
-      case VM_END: ended = true; break;
-      case VM_LD: case VM_ADD: case VM_MUL: if (!ok(a)) { why = "operand out of range"; return false; } break;
-      case VM_FMA: case VM_FMAC: case VM_ACCW: case VM_LDMUL:
-        if (!ok(a) || !ok(b)) { why = "operand out of range"; return false; } break;
-      case VM_RCP: case VM_ABS: break;
-      case VM_ST: if (a >= VM_KFLAG || int(a) >= n_regs || int(a) < n_lines) { why = "store target out of range"; return false; } break;
-      default: why = "unknown opcode"; return false;
+    const uint32_t lo = ins[i].x, hi = ins[i].y;
+    const uint32_t a = lo & 1023u, b = (lo >> 10) & 1023u, d = (lo >> 20) & 1023u, sp = hi & 7u;
+    if ((hi >> 4) || sp > VM_SP_END) { why = "bad special field"; return false; }
+    // both operands are read by every instruction
+    if (!ok(a) || !ok(b)) { why = "operand out of range"; return false; }
+    if (d != 0 && (int(d) < n_lines || int(d) >= n_regs)) { why = "store target out of range"; return false; }
+    // the interpreter loads an instruction's operands before the previous
+    // instruction stores
+    if (i > 0) {
+      const uint32_t pd = (ins[i - 1].x >> 20) & 1023u;
+      if (pd != 0 && (a == pd || b == pd)) { why = "instruction reads the register the previous one writes"; return false; }
     }
-    if (ended) break;
+    if (sp == VM_SP_END) {
+      if (i != n_ins - 1) { why = "END is not the last instruction"; return false; }
+      return true;
+    }
   }
-  if (!ended) { why = "program without END"; return false; }
-  return true;
+  why = "program without END";
+  return false;
 }
 
 extern "C" int qed_programs_load(qed_ctx *c, const void *data, size_t bytes, int *count) {
   if (!c || !data) return set_err(QED_EINVAL, "ctx/data is NULL");
   const unsigned char *p = static_cast<const unsigned char *>(data), *end = p + bytes;
-  if (bytes < 16 || std::memcmp(p, "QEDVM001", 8) != 0) return set_err(QED_EINVAL, "not a qed program file");
+  if (bytes < 16 || std::memcmp(p, "QEDVM002", 8) != 0) return set_err(QED_EINVAL, "not a qed program file");
   uint32_t n = 0;
   std::memcpy(&n, p + 8, 4);
   p += 16;
-  struct Rec { qed_ctx::VmProg pr; const uint32_t *ins; const double *kon; };
+  struct Rec { qed_ctx::VmProg pr; const unsigned char *ins; const unsigned char *kon; };
   std::vector<Rec> recs;
   size_t words = 0, kons = 0;
   for (uint32_t i = 0; i < n; ++i) {
@@ -278,34 +293,34 @@ extern "C" int qed_programs_load(qed_ctx *c, const void *data, size_t bytes, int
     p += 88;
     r.pr.n_lines = m[0]; r.pr.n_regs = m[1]; r.pr.n_ins = m[2]; r.pr.n_kon = m[3];
     if (m[0] < 3 || m[0] > 3 * QED_MAX_LOOPS || m[0] % 3 || m[2] < 1 || m[3] < 0) return set_err(QED_EINVAL, "bad program header");
-    const size_t ib = (size_t(m[2]) + (m[2] & 1)) * 4, kb = size_t(m[3]) * 8;
+    const size_t ib = size_t(m[2]) * 8, kb = size_t(m[3]) * 8;
     if (size_t(end - p) < ib + kb) return set_err(QED_EINVAL, "truncated program file");
-    r.ins = reinterpret_cast<const uint32_t *>(p);
-    r.kon = reinterpret_cast<const double *>(p + ib);
+    r.ins = p;
+    r.kon = p + ib;
     std::string why;
-    std::vector<uint32_t> tmp(r.ins, r.ins + m[2]);
+    std::vector<uint2> tmp(static_cast<size_t>(m[2]));
+    std::memcpy(tmp.data(), r.ins, ib);
     if (!vm_check(tmp.data(), m[2], m[1], m[3], m[0], why)) return set_err(QED_EINVAL, "program " + r.pr.name + ": " + why);
     p += ib + kb;
-    words += (size_t(m[2]) + 3) & ~size_t(3);
+    words += (((size_t(m[2]) + 1) & ~size_t(1)) + 8) * 2;  // 32-bit words: pairs, plus 4 zero groups
     kons += size_t(m[3]);
     recs.push_back(r);
   }
   CUDA_TRY(cudaSetDevice(c->device));
-  // one buffer per file: instruction words (each program END-padded to a
-  // multiple of 4 words, 16-byte aligned), then the constants
+  // one buffer per file: instructions (each program padded with zero words
+  // to an even count, so 16-byte aligned, then four zero groups that the
+  // interpreter's look-ahead reads but never executes: END comes first and
+  // a zero word names register 0), then the constants
   void *buf = nullptr;
-  // 16 spare bytes at the end: the interpreter loads the instruction group
-  // after the current one before executing it, so the last program's END
-  // group is followed by at least 16 readable bytes
   const size_t wbytes = words * 4, total = wbytes + kons * 8 + 16;
   CUDA_TRY(cudaMalloc(&buf, total));
   std::vector<unsigned char> host(total, 0);
   size_t wo = 0, ko = wbytes;
   std::vector<qed_ctx::VmProg> progs;
   for (auto &r : recs) {
-    std::memcpy(host.data() + wo, r.ins, size_t(r.pr.n_ins) * 4);
-    r.pr.d_ins = reinterpret_cast<const uint32_t *>(static_cast<unsigned char *>(buf) + wo);
-    wo += ((size_t(r.pr.n_ins) + 3) & ~size_t(3)) * 4;
+    std::memcpy(host.data() + wo, r.ins, size_t(r.pr.n_ins) * 8);
+    r.pr.d_ins = reinterpret_cast<const uint2 *>(static_cast<unsigned char *>(buf) + wo);
+    wo += (((size_t(r.pr.n_ins) + 1) & ~size_t(1)) + 8) * 8;
     std::memcpy(host.data() + ko, r.kon, size_t(r.pr.n_kon) * 8);
     r.pr.d_kon = reinterpret_cast<const double *>(static_cast<unsigned char *>(buf) + ko);
     ko += size_t(r.pr.n_kon) * 8;
@@ -468,7 +483,9 @@ static int vm_launch(const qed_ctx *c, const qed_ctx::VmProg &pr, const void *fn
   L.code = VmCode{pr.d_ins, pr.d_kon, pr.n_kon, pr.n_regs};
   const size_t cap = 220 * 1024;       // dynamic part; the kernels' static shared memory is a few KB
   auto bytes = [&](int t) {
-    return dd_frame ? vm_smem_bytes<dd>(pr.n_kon, pr.n_regs, t) : vm_smem_bytes<double>(pr.n_kon, pr.n_regs, t);
+    if (dd_frame) return vm_smem_bytes<dd, 1>(pr.n_kon, pr.n_regs, t);
+    return c->vm_points == 2 ? vm_smem_bytes<double, 2>(pr.n_kon, pr.n_regs, t)
+                             : vm_smem_bytes<double, 1>(pr.n_kon, pr.n_regs, t);
   };
   int T = threads;
   while (T > 32 && bytes(T) > cap) T /= 2;
@@ -481,7 +498,9 @@ static int vm_launch(const qed_ctx *c, const qed_ctx::VmProg &pr, const void *fn
   L.blocks = std::max(1, occ) * c->sms;
   return QED_OK;
 }
-static const VmKernelSet &vm_kernels(const qed_diag *d) { return g_vm_kernels[d->N / 3 - 1]; }
+static const VmKernelSet &vm_kernels(const qed_diag *d) {
+  return g_vm_kernels[d->ctx->vm_points == 2 ? 1 : 0][d->N / 3 - 1];
+}
 
 static int fold(qed_ctx *c, int blocks, qed_result *r, bool add_flagged_as_count);
 static void finish(qed_result *r);

@@ -5,9 +5,10 @@ numpy interpretation of it reproduces the oracle's subtracted integrand
 are the oracle's, stored by tests/golden/make_four_loop.py at the Eq. (1)
 points of fixed Philox counters.
 
-Instruction word: op[0:4) a[4:14) b[14:24); operand >= 512 selects a
-constant.  Ops: END LD ADD MUL FMA(acc*a+b) FMAC(a*b+acc) RCP ABS ST ACCW
-LDMUL, in that order."""
+Instruction (64 bits): lo = A | B << 10 | D << 20 | XA << 30 | ZO << 31,
+hi = SPEC | NOCOMP << 3; operand >= 512 selects a constant.  Unless NOCOMP:
+X = XA ? A : acc, O = XA ? acc : A, acc = X * B + (ZO ? O : 0); then SPEC
+(1 RCP, 2 ABS, 3 ACCW: W += |A| e(B), 4 END); then D != 0 stores acc."""
 import struct
 from pathlib import Path
 
@@ -24,7 +25,7 @@ GOLDEN4 = ROOT / "tests" / "golden" / "four_loop_points.txt"
 
 def read_programs(path):
     data = path.read_bytes()
-    assert data[:8] == b"QEDVM001"
+    assert data[:8] == b"QEDVM002"
     (count,) = struct.unpack_from("<I", data, 8)
     off = 16
     progs = {}
@@ -33,8 +34,8 @@ def read_programs(path):
         n_lines, n_regs, n_ins, n_kon = struct.unpack_from("<4i", data, off + 64)
         (flops,) = struct.unpack_from("<d", data, off + 80)
         off += 88
-        ins = np.frombuffer(data, dtype="<u4", count=n_ins, offset=off)
-        off += 4 * (n_ins + (n_ins & 1))
+        ins = np.frombuffer(data, dtype="<u8", count=n_ins, offset=off)
+        off += 8 * n_ins
         kon = np.frombuffer(data, dtype="<f8", count=n_kon, offset=off)
         off += 8 * n_kon
         progs[name] = dict(n_lines=n_lines, n_regs=n_regs, ins=ins, kon=kon, flops=flops)
@@ -43,7 +44,7 @@ def read_programs(path):
 
 
 def interpret(p, z, dtype=np.float64):
-    """acc / register machine of the generator, vectorised over points."""
+    """The fused accumulator / register machine, vectorised over points."""
     z = np.asarray(z, dtype=dtype)
     B, N = z.shape
     R = np.zeros((p["n_regs"], B), dtype=dtype)
@@ -56,34 +57,34 @@ def interpret(p, z, dtype=np.float64):
     W = np.zeros(B, dtype=dtype)
 
     def get(x):
-        return (K[x - 512], abs(K[x - 512])) if x >= 512 else (R[x], E[x])
+        if x >= 512:
+            return np.full(B, K[x - 512], dtype=dtype), np.full(B, abs(K[x - 512]), dtype=dtype)
+        return R[x], E[x]
 
     for w in p["ins"].tolist():
-        op, a, b = w & 15, (w >> 4) & 1023, (w >> 14) & 1023
-        if op == 0:
-            return acc, W
-        if op == 1:
-            v, e = get(a); acc = np.broadcast_to(v, (B,)).astype(dtype); ae = np.broadcast_to(e, (B,)).astype(dtype)
-        elif op == 2:
-            v, e = get(a); acc = acc + v; ae = ae + e
-        elif op == 3:
-            v, e = get(a); acc = acc * v; ae = ae * e
-        elif op == 4:
-            (v, e), (u, f) = get(a), get(b); acc = acc * v + u; ae = ae * e + f
-        elif op == 5:
-            (v, e), (u, f) = get(a), get(b); acc = v * u + acc; ae = e * f + ae
-        elif op == 6:
-            acc = 1 / acc; ae = np.abs(acc)
-        elif op == 7:
+        lo, hi = w & 0xFFFFFFFF, w >> 32
+        a, b, d = lo & 1023, (lo >> 10) & 1023, (lo >> 20) & 1023
+        xa, zo, spec, nocomp = (lo >> 30) & 1, (lo >> 31) & 1, hi & 7, (hi >> 3) & 1
+        (va, ea), (vb, eb) = get(a), get(b)
+        if not nocomp:
+            X, eX = (va, ea) if xa else (acc, ae)
+            O, eO = (acc, ae) if xa else (va, ea)
+            Z, eZ = (O, eO) if zo else (0, 0)
+            acc, ae = X * vb + Z, eX * eb + eZ
+        if spec == 1:
+            acc = 1 / acc
             ae = np.abs(acc)
-        elif op == 8:
-            R[a] = acc; E[a] = ae
-        elif op == 9:
-            (v, e), (u, f) = get(a), get(b); W = W + np.abs(v) * f
-        elif op == 10:
-            (v, e), (u, f) = get(a), get(b); acc = v * u; ae = e * f
-        else:
-            raise AssertionError(f"bad opcode {op}")
+        elif spec == 2:
+            ae = np.abs(acc)
+        elif spec == 3:
+            W = W + np.abs(va) * eb
+        elif spec == 4:
+            return acc, W
+        elif spec != 0:
+            raise AssertionError(f"bad special {spec}")
+        if d:
+            R[d] = acc
+            E[d] = ae
     raise AssertionError("program without END")
 
 
@@ -106,18 +107,20 @@ def test_programs_well_formed(n):
     for name, p in progs.items():
         assert p["n_lines"] == 3 * n and p["n_lines"] <= p["n_regs"] <= 512 and len(p["kon"]) <= 512
         ins = p["ins"]
-        op, a, b = ins & 15, (ins >> 4) & 1023, (ins >> 14) & 1023
-        assert (ins >> 24).max() == 0 and op.max() <= 10
-        end = int(np.argmax(op == 0))
-        assert op[end] == 0
+        lo, hi = ins & 0xFFFFFFFF, ins >> 32
+        a, b, d = lo & 1023, (lo >> 10) & 1023, (lo >> 20) & 1023
+        spec = hi & 7
+        assert (hi >> 4).max() == 0 and spec.max() <= 4
+        end = int(np.argmax(spec == 4))
+        assert spec[end] == 4
         ok = lambda x: np.where(x >= 512, x - 512 < len(p["kon"]), x < p["n_regs"])   # noqa: E731
-        for o in (1, 2, 3):
-            assert ok(a[:end][op[:end] == o]).all(), name
-        for o in (4, 5, 9, 10):
-            sel = op[:end] == o
-            assert ok(a[:end][sel]).all() and ok(b[:end][sel]).all(), name
-        st = a[:end][op[:end] == 8]
+        assert ok(a[:end + 1]).all() and ok(b[:end + 1]).all(), name
+        st = d[:end + 1][d[:end + 1] != 0]
         assert ((st >= p["n_lines"]) & (st < p["n_regs"])).all(), name
+        # END last; no instruction reads the register the previous one writes
+        assert end == len(ins) - 1, name
+        prev = d[:-1]
+        assert not np.any((prev != 0) & ((a[1:] == prev) | (b[1:] == prev))), name
 
 
 @pytest.mark.parametrize("n,sel", [(2, None), (3, [0, 9, 19, 27])])
