@@ -132,7 +132,7 @@ int qed_gauge_class(const qed_graph *g, int kmn[3]);
  * 500 GB.  From four loops on, the generator therefore writes each
  * integrand as a program for the library's interpreter kernels instead of
  * source to compile.  data/bytes: the contents of a program file written by
- * the generator (vm_n<n>.bin: "QEDVM002", count, then per program its graph
+ * the generator (vm_n<n>.bin: "QEDVM003", count, then per program its graph
  * name, line count, register count, 64-bit instructions and constants), in
  * host memory, owned by the caller and copied to the device.  Every
  * instruction is checked against its program's register and constant counts

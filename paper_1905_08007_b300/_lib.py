@@ -197,8 +197,8 @@ QED_CTX_PREFER_PROGRAMS = 1
 
 
 def program_files():
-    """Bytecode integrand files written by the build (vm_n<n>.bin)."""
-    return sorted((_HERE / "csrc" / "_gen").glob("vm_n*.bin"))
+    """Bytecode integrand files written by the build (vm_n<n>.bin.z, zlib)."""
+    return sorted((_HERE / "csrc" / "_gen").glob("vm_n*.bin.z"))
 
 
 class Context:
@@ -218,8 +218,9 @@ class Context:
         self.device = device
         self.n_programs = 0
         if programs:
+            import zlib
             for f in program_files():
-                self.programs_load(f.read_bytes())
+                self.programs_load(zlib.decompress(f.read_bytes()))
         if threads is not None or blocks is not None:
             self.set_launch(threads or 256, blocks or 0)
         if threshold is not None:

@@ -11,14 +11,17 @@ Steps:
    kernels) for sm_103a, in parallel, and link them into ``libqedmc.so`` next
    to this file;
 3. run the generator's bytecode back end for the program orders: it writes
-   ``csrc/_gen/vm_n<n>.bin`` (one program per mirror-reduced graph), which the
-   library's interpreter kernels evaluate (four loops and up have no compiled
-   integrands; the lower orders are there to compare the two paths).
+   ``csrc/_gen/vm_n<n>.bin`` (one program per mirror-reduced graph; at five
+   loops the 64 graphs of ``five_loop_subset.txt``), stored zlib-compressed as
+   ``vm_n<n>.bin.z``; the library's interpreter kernels evaluate them (four
+   loops and up have no compiled integrands; the lower orders are there to
+   compare the two paths).
 """
 from __future__ import annotations
 
 import argparse
 import re
+import zlib
 from concurrent.futures import ThreadPoolExecutor
 import hashlib
 import os
@@ -35,7 +38,7 @@ INCLUDE = ROOT / "include"
 BUILD = ROOT / "_build"
 LIB = PKG / "libqedmc.so"
 DEFAULT_ORDERS = (1, 2, 3)
-DEFAULT_PROGRAM_ORDERS = (2, 3, 4)
+DEFAULT_PROGRAM_ORDERS = (2, 3, 4, 5)      # 5: the 64-graph workload of five_loop_subset.txt
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -76,17 +79,29 @@ def build_programs(orders=DEFAULT_PROGRAM_ORDERS, force=False):
     orders = tuple(int(o) for o in orders)
     BUILD.mkdir(exist_ok=True)
     GEN.mkdir(exist_ok=True)
-    outs = [GEN / f"vm_n{n}.bin" for n in orders]
+    outs = [GEN / f"vm_n{n}.bin.z" for n in orders]
     stamp = BUILD / "programs.stamp"
-    key = _digest(GEN_SRC, extra=repr(orders))
+    key = _digest(GEN_SRC + [PKG / "five_loop_subset.txt"], extra=repr(orders))
     if not force and all(o.exists() for o in outs) and stamp.exists() and stamp.read_text() == key:
         return outs
-    for old in GEN.glob("vm_n*.bin"):
+    for old in list(GEN.glob("vm_n*.bin")) + list(GEN.glob("vm_n*.bin.z")):
         old.unlink()
     if orders:
-        _run([_generator(), GEN] + [f"v{n}" for n in orders])
+        subset = PKG / "five_loop_subset.txt"
+        _run([_generator(), GEN] + [f"v{n}@{subset}" if n == 5 else f"v{n}" for n in orders])
+    for n in orders:
+        compress_programs(GEN / f"vm_n{n}.bin")
     stamp.write_text(key)
     return outs
+
+
+def compress_programs(raw):
+    """vm_n<n>.bin -> vm_n<n>.bin.z (zlib; programs shrink about 6x)."""
+    raw = Path(raw)
+    z = raw.with_name(raw.name + ".z")
+    z.write_bytes(zlib.compress(raw.read_bytes(), 6))
+    raw.unlink()
+    return z
 
 
 def build(orders=DEFAULT_ORDERS, force=False, verbose_ptxas=False, jobs=None,

@@ -44,8 +44,10 @@ struct BatchParams {
   unsigned long long *cnt;          // [n_items][2]  flagged, (unused)
   uint32_t *lists;                  // [n_items][list_cap] flagged offsets
   uint32_t list_cap;
-  double *part_dd;                  // [n_items][4]  double-double moments
-  unsigned long long *cnt_dd;       // [n_items][2]  (unused), unstable
+  double *part_dd;                  // [n_items * dd_tiles][4]  double-double moments
+  unsigned long long *cnt_dd;       // [n_items * dd_tiles][2]  (unused), unstable
+  uint32_t dd_tiles;                // double-double tiles per item (1: one block per item)
+  unsigned int *next_tile;          // tile counter of the bytecode dd pass, zeroed every round
 };
 
 __device__ __forceinline__ KParams batch_kparams(const BatchParams &B, const BatchDiag &D) {

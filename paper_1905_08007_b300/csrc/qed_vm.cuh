@@ -26,21 +26,21 @@
 #include "qed_batch.cuh"
 
 // Instruction (64 bits, written by the generator's fuse step):
-//   lo = A | B << 10 | D << 20 | XA << 30 | ZO << 31,  hi = SPEC | NOCOMP << 3
+//   lo = A | B << 11 | D << 22,  hi = XA | ZO << 1 | SPEC << 2 | NOCOMP << 5
 //   1. unless NOCOMP:  X = XA ? A : acc,  O = XA ? acc : A,
 //                      acc = X * B + (ZO ? O : 0)          (e lane alike)
 //   2. SPEC 1: acc = 1 / acc, e = |acc|;  2: e = |acc|;  3: W += |A.v| * B.e;
 //      4: end
 //   3. store acc in R[D] (D = 0: in the spare register)
-// Operands A, B: a register index, or 512 + a constant index.  Every
+// Operands A, B: a register index, or 1024 + a constant index.  Every
 // instruction reads both operands (the generator names the constants 0 or 1
 // where one is unused), so the common path has no branch on the operation.
-#define VM_KFLAG 512u
+#define VM_KFLAG 1024u
 #define VM_SP_RCP 1u
 #define VM_SP_ABS 2u
 #define VM_SP_ACCW 3u
 #define VM_SP_END 4u
-#define VM_NOCOMP 8u
+#define VM_NOCOMP 32u
 
 struct VmCode {
   const uint2 *ins;       // instructions (lo, hi), END-padded to an even count
@@ -158,7 +158,7 @@ struct VmFrame {
                                        const R (&vb)[P], const E (&eb)[P], R (&acc)[P], E (&ae)[P],
                                        double (&W)[P]) {
     if (!(hi & VM_NOCOMP)) {
-      const bool xa = (lo >> 30) & 1u, zo = lo >> 31;
+      const bool xa = hi & 1u, zo = (hi >> 1) & 1u;
 #pragma unroll
       for (int p = 0; p < P; ++p) {
         const R X = xa ? va[p] : acc[p], O = xa ? acc[p] : va[p];
@@ -167,7 +167,7 @@ struct VmFrame {
         ae[p] = eX * eb[p] + (zo ? eO : E(0));
       }
     }
-    const uint32_t sp = hi & 7u;
+    const uint32_t sp = (hi >> 2) & 7u;
     if (sp) {
       if (sp == VM_SP_END) return true;
 #pragma unroll
@@ -185,7 +185,7 @@ struct VmFrame {
         }
       }
     }
-    const uint32_t d = (lo >> 20) & 1023u;
+    const uint32_t d = lo >> 22;
     put(d ? d : spare, acc, ae);
     return false;
   }
@@ -218,14 +218,14 @@ struct VmFrame {
     uint4 g0 = __ldg(ip), g1 = __ldg(ip + 1), g2 = __ldg(ip + 2), g3 = __ldg(ip + 3);
     R va[P], vb[P], na[P], nb[P];
     E ea[P], eb[P], nea[P], neb[P];
-    get(g0.x & 1023u, va, ea);
-    get((g0.x >> 10) & 1023u, vb, eb);
+    get(g0.x & 2047u, va, ea);
+    get((g0.x >> 11) & 2047u, vb, eb);
     for (;; ++ip) {
-      get(g0.z & 1023u, na, nea);
-      get((g0.z >> 10) & 1023u, nb, neb);
+      get(g0.z & 2047u, na, nea);
+      get((g0.z >> 11) & 2047u, nb, neb);
       if (step(g0.x, g0.y, va, ea, vb, eb, acc, ae, W)) break;
-      get(g1.x & 1023u, va, ea);
-      get((g1.x >> 10) & 1023u, vb, eb);
+      get(g1.x & 2047u, va, ea);
+      get((g1.x >> 11) & 2047u, vb, eb);
       if (step(g0.z, g0.w, na, nea, nb, neb, acc, ae, W)) break;
       g0 = g1;
       g1 = g2;
@@ -501,30 +501,45 @@ __global__ void __launch_bounds__(256) k_batch_vm_fp64(BatchParams B) {
   }
 }
 
+// The double-double pass over the items' flagged lists, in tiles of one
+// point per thread: tile t covers entries [k * blockDim, (k + 1) * blockDim)
+// of item t / dd_tiles's list (k = t % dd_tiles), blocks take tiles from a
+// device counter, and every tile writes its own partial (zeros when the
+// list is shorter), which the host folds per item in tile order.
 template <int N>
 __global__ void __launch_bounds__(256) k_batch_vm_dd(BatchParams B) {
   extern __shared__ __align__(16) unsigned char vsm[];
-  for (unsigned int it = blockIdx.x; it < B.n_items; it += gridDim.x) {
-    const BatchItem I = B.items[it];
+  __shared__ unsigned int s_tile;
+  const unsigned int n_tiles = B.n_items * B.dd_tiles;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(B.next_tile, 1u);
+    __syncthreads();
+    const unsigned int t = s_tile;
+    __syncthreads();
+    if (t >= n_tiles) break;
+    const unsigned int it = t / B.dd_tiles, k = t % B.dd_tiles;
     const unsigned long long nflag = B.cnt[2 * size_t(it)];
-    if (nflag == 0) {
+    const uint64_t total = nflag < B.list_cap ? nflag : B.list_cap;
+    const uint64_t start = uint64_t(k) * blockDim.x;
+    if (start >= total) {
       if (threadIdx.x == 0) {
-        double *p = B.part_dd + 4 * size_t(it);
+        double *p = B.part_dd + 4 * size_t(t);
         p[0] = p[1] = p[2] = p[3] = 0.0;
-        B.cnt_dd[2 * size_t(it)] = 0;
-        B.cnt_dd[2 * size_t(it) + 1] = 0;
+        B.cnt_dd[2 * size_t(t)] = 0;
+        B.cnt_dd[2 * size_t(t) + 1] = 0;
       }
       continue;
     }
+    const BatchItem I = B.items[it];
     const BatchDiag &D = B.diags[I.diag];
     const KParams K = batch_kparams(B, D);
     const VmCode C = {D.vins, D.vkon, D.vnk, D.vnr};
     VmFrame<dd, 1> fr;
     fr.setup(C, vsm);
-    const uint64_t total = nflag < B.list_cap ? nflag : B.list_cap;
     KSum sw, sw2;
     unsigned long long nunst = 0;
-    for (uint64_t i = threadIdx.x; i < total; i += blockDim.x) {
+    const uint64_t i = start + threadIdx.x;
+    if (i < total) {
       const uint32_t off = B.lists[size_t(it) * B.list_cap + i];
       double z[N];
       const double lp = draw_point<N>(I.begin + off, K, K.F, K.G, K.invdeg, z);
@@ -534,12 +549,10 @@ __global__ void __launch_bounds__(256) k_batch_vm_dd(BatchParams B) {
       for (int L = 0; L < N; ++L) zd[0][L] = dd{z[L], 0.0};
       fr.template eval<N>(C, zd, f, ab);
       const double w = (f[0].hi + f[0].lo) * exp(-lp);
-      if (!isfinite(w) || !(rel_err_estimate(f[0].hi, ab[0], 1.2325951644078309e-32) <= K.thresh)) { ++nunst; continue; }
-      sw.add(w);
-      sw2.add(w * w);
+      if (!isfinite(w) || !(rel_err_estimate(f[0].hi, ab[0], 1.2325951644078309e-32) <= K.thresh)) ++nunst;
+      else { sw.add(w); sw2.add(w * w); }
     }
-    block_reduce_store(sw, sw2, 0ull, nunst, B.part_dd, B.cnt_dd, it);
-    __syncthreads();
+    block_reduce_store(sw, sw2, 0ull, nunst, B.part_dd, B.cnt_dd, t);
   }
 }
 

@@ -13,7 +13,7 @@
 //   register file R[0..n_regs) of (v, e) pairs (z[0..N) preloaded in
 //   R[0..N) with e = z), and a double W that collects the monomial
 //   absolute sum of the integrand;
-//   per program: a table K of constants (operand flag 512 selects K, with
+//   per program: a table K of constants (operand flag 1024 selects K, with
 //   e = |K|).
 //   The e lane follows the value lane through +, *, fma with the operands'
 //   e values; for the quantities whose magnitude the compiled path takes as
@@ -35,10 +35,10 @@
 //   ST a        R[a] = acc
 //   ACCW a b    W += |a.v| * b.e
 //   LDMUL a b   acc = a * b
-// (operands: a register index, or 512 + a constant index), and fuses them
+// (operands: a register index, or 1024 + a constant index), and fuses them
 // into 64-bit instructions that the interpreter executes without a dispatch
 // on the operation:
-//   lo = A | B << 10 | D << 20 | XA << 30 | ZO << 31,  hi = SPEC | NOCOMP << 3
+//   lo = A | B << 11 | D << 22,  hi = XA | ZO << 1 | SPEC << 2 | NOCOMP << 5
 //   1. unless NOCOMP:  X = XA ? A : acc,  O = XA ? acc : A,
 //                      acc = X * B + (ZO ? O : 0)           (e lane alike)
 //   2. SPEC 1 RCP: acc = 1 / acc, e = |acc|;  2 ABS: e = |acc|;
@@ -66,21 +66,20 @@
 namespace qvm {
 
 enum Op : uint32_t { END = 0, LD, ADD, MUL, FMA, FMAC, RCP, ABS, ST, ACCW, LDMUL };
-constexpr int KFLAG = 512;          // operand >= KFLAG: constant K[operand - KFLAG]
-constexpr int MAX_REGS = 512;
-constexpr int MAX_KON = 512;
+constexpr int KFLAG = 1024;         // operand >= KFLAG: constant K[operand - KFLAG]
+constexpr int MAX_REGS = 1023;
+constexpr int MAX_KON = 1024;
 
 inline uint32_t enc(Op op, int a = 0, int b = 0) {
-  return uint32_t(op) | (uint32_t(a) << 4) | (uint32_t(b) << 14);
+  return uint32_t(op) | (uint32_t(a) << 4) | (uint32_t(b) << 15);
 }
 
 enum : uint32_t { SP_NONE = 0, SP_RCP = 1, SP_ABS = 2, SP_ACCW = 3, SP_END = 4 };
-constexpr uint32_t NOCOMP = 8u;
+constexpr uint32_t NOCOMP = 32u;
 
 inline uint64_t word(int A, int B, int D, bool xa, bool zo, uint32_t spec, bool nocomp) {
-  const uint32_t lo = uint32_t(A) | (uint32_t(B) << 10) | (uint32_t(D) << 20) | (uint32_t(xa) << 30) |
-                      (uint32_t(zo) << 31);
-  const uint32_t hi = spec | (nocomp ? NOCOMP : 0u);
+  const uint32_t lo = uint32_t(A) | (uint32_t(B) << 11) | (uint32_t(D) << 22);
+  const uint32_t hi = uint32_t(xa) | (uint32_t(zo) << 1) | (spec << 2) | (nocomp ? NOCOMP : 0u);
   return uint64_t(lo) | (uint64_t(hi) << 32);
 }
 
@@ -399,7 +398,7 @@ class Compiler {
     bool open = false;          // last instruction can still take a special / store
     bool has_spec = false, has_st = false;
     for (uint32_t w : P.ins) {
-      const int op = int(w & 15u), a = int((w >> 4) & 1023u), b = int((w >> 14) & 1023u);
+      const int op = int(w & 15u), a = int((w >> 4) & 2047u), b = int((w >> 15) & 2047u);
       auto put = [&](uint64_t x, bool can_extend) {
         C.push_back(x);
         open = can_extend;
@@ -416,12 +415,12 @@ class Compiler {
         case RCP:
         case ABS: {
           const uint32_t sp = op == RCP ? SP_RCP : SP_ABS;
-          if (open && !has_spec && !has_st) { C.back() |= uint64_t(sp) << 32; has_spec = true; }
+          if (open && !has_spec && !has_st) { C.back() |= uint64_t(sp) << 34; has_spec = true; }
           else { put(word(zero, one, 0, false, false, sp, true), true); has_spec = true; }
           break;
         }
         case ST:
-          if (open && !has_st) { C.back() |= uint64_t(uint32_t(a) << 20); has_st = true; }
+          if (open && !has_st) { C.back() |= uint64_t(uint32_t(a)) << 22; has_st = true; }
           else { put(word(zero, one, a, false, false, SP_NONE, true), false); }
           break;
         case ACCW: put(word(a, b, 0, false, false, SP_ACCW, true), false); break;
@@ -434,8 +433,8 @@ class Compiler {
     out.reserve(C.size() + C.size() / 8);
     for (size_t i = 0; i < C.size(); ++i) {
       if (i > 0) {
-        const uint32_t d = uint32_t(C[i - 1] >> 20) & 1023u;
-        const uint32_t a = uint32_t(C[i]) & 1023u, b = uint32_t(C[i] >> 10) & 1023u;
+        const uint32_t d = uint32_t(C[i - 1] >> 22) & 1023u;
+        const uint32_t a = uint32_t(C[i]) & 2047u, b = uint32_t(C[i] >> 11) & 2047u;
         if (d != 0 && (a == d || b == d)) out.push_back(word(zero, one, 0, false, false, SP_NONE, true));
       }
       out.push_back(C[i]);
@@ -584,7 +583,7 @@ class Compiler {
 // ---------------------------------------------------------------------------
 // program file
 // ---------------------------------------------------------------------------
-// Layout (little endian): "QEDVM002", u32 count, u32 0, then per program a
+// Layout (little endian): "QEDVM003", u32 count, u32 0, then per program a
 // 64-byte name, i32 n_lines, n_regs, n_ins, n_kon, f64 flops, the n_ins
 // 64-bit instructions and the constants.
 struct Entry {
@@ -596,7 +595,7 @@ struct Entry {
 inline void write_programs(const std::string &path, const std::vector<Entry> &es) {
   FILE *f = fopen(path.c_str(), "wb");
   if (!f) { fprintf(stderr, "vm: cannot write %s\n", path.c_str()); exit(1); }
-  fwrite("QEDVM002", 1, 8, f);
+  fwrite("QEDVM003", 1, 8, f);
   const uint32_t hdr[2] = {uint32_t(es.size()), 0u};
   fwrite(hdr, 4, 2, f);
   for (auto &e : es) {

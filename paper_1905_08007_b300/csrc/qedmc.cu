@@ -247,19 +247,19 @@ extern "C" int qed_ctx_set_threshold(qed_ctx *c, double rel) {
 // counts here, so that the interpreter's shared-memory accesses stay inside
 // the frame the host sized for it.
 static bool vm_check(const uint2 *ins, int n_ins, int n_regs, int n_kon, int n_lines, std::string &why) {
-  if (n_regs < n_lines || n_regs > 511 || n_kon < 0 || n_kon > 512 || n_ins < 1) { why = "program sizes out of range"; return false; }
+  if (n_regs < n_lines || n_regs > 1023 || n_kon < 0 || n_kon > 1024 || n_ins < 1) { why = "program sizes out of range"; return false; }
   auto ok = [&](uint32_t a) { return a < VM_KFLAG ? int(a) < n_regs : int(a - VM_KFLAG) < n_kon; };
   for (int i = 0; i < n_ins; ++i) {
     const uint32_t lo = ins[i].x, hi = ins[i].y;
-    const uint32_t a = lo & 1023u, b = (lo >> 10) & 1023u, d = (lo >> 20) & 1023u, sp = hi & 7u;
-    if ((hi >> 4) || sp > VM_SP_END) { why = "bad special field"; return false; }
+    const uint32_t a = lo & 2047u, b = (lo >> 11) & 2047u, d = lo >> 22, sp = (hi >> 2) & 7u;
+    if ((hi >> 6) || sp > VM_SP_END) { why = "bad special field"; return false; }
     // both operands are read by every instruction
     if (!ok(a) || !ok(b)) { why = "operand out of range"; return false; }
     if (d != 0 && (int(d) < n_lines || int(d) >= n_regs)) { why = "store target out of range"; return false; }
     // the interpreter loads an instruction's operands before the previous
     // instruction stores
     if (i > 0) {
-      const uint32_t pd = (ins[i - 1].x >> 20) & 1023u;
+      const uint32_t pd = ins[i - 1].x >> 22;
       if (pd != 0 && (a == pd || b == pd)) { why = "instruction reads the register the previous one writes"; return false; }
     }
     if (sp == VM_SP_END) {
@@ -274,7 +274,7 @@ static bool vm_check(const uint2 *ins, int n_ins, int n_regs, int n_kon, int n_l
 extern "C" int qed_programs_load(qed_ctx *c, const void *data, size_t bytes, int *count) {
   if (!c || !data) return set_err(QED_EINVAL, "ctx/data is NULL");
   const unsigned char *p = static_cast<const unsigned char *>(data), *end = p + bytes;
-  if (bytes < 16 || std::memcmp(p, "QEDVM002", 8) != 0) return set_err(QED_EINVAL, "not a qed program file");
+  if (bytes < 16 || std::memcmp(p, "QEDVM003", 8) != 0) return set_err(QED_EINVAL, "not a qed program file");
   uint32_t n = 0;
   std::memcpy(&n, p + 8, 4);
   p += 16;
@@ -838,16 +838,20 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
   }
   // device and pinned buffers
   DevBuf dd_diags, dd_items, dd_next, dd_part, dd_cnt, dd_lists, dd_pdd, dd_cdd;
+  // bytecode batches: the dd pass runs in tiles of one point per thread
+  const uint32_t dd_tiles = vmb ? uint32_t((chunk + uint64_t(thr2) - 1) / uint64_t(thr2)) : 1u;
+  const size_t n_dd = size_t(n_items) * dd_tiles;
   HostBuf h_items, h_out;
   CUDA_TRY(cudaMalloc(&dd_diags.p, sizeof(BatchDiag) * k));
   CUDA_TRY(cudaMalloc(&dd_items.p, sizeof(BatchItem) * n_items));
-  CUDA_TRY(cudaMalloc(&dd_next.p, sizeof(unsigned int)));
+  CUDA_TRY(cudaMalloc(&dd_next.p, 2 * sizeof(unsigned int)));
   CUDA_TRY(cudaMalloc(&dd_part.p, sizeof(double) * 4 * n_items));
   CUDA_TRY(cudaMalloc(&dd_cnt.p, sizeof(unsigned long long) * 2 * n_items));
-  CUDA_TRY(cudaMalloc(&dd_pdd.p, sizeof(double) * 4 * n_items));
-  CUDA_TRY(cudaMalloc(&dd_cdd.p, sizeof(unsigned long long) * 2 * n_items));
+  CUDA_TRY(cudaMalloc(&dd_pdd.p, sizeof(double) * 4 * n_dd));
+  CUDA_TRY(cudaMalloc(&dd_cdd.p, sizeof(unsigned long long) * 2 * n_dd));
   CUDA_TRY(cudaMalloc(&dd_lists.p, sizeof(uint32_t) * size_t(list_cap) * n_items));
-  const size_t out_bytes = n_items * (8 * sizeof(double) + 4 * sizeof(unsigned long long));
+  const size_t out_bytes = n_items * (4 * sizeof(double) + 2 * sizeof(unsigned long long)) +
+                           n_dd * (4 * sizeof(double) + 2 * sizeof(unsigned long long));
   CUDA_TRY(cudaMallocHost(&h_items.p, sizeof(BatchItem) * n_items));
   CUDA_TRY(cudaMallocHost(&h_out.p, out_bytes));
   std::vector<BatchDiag> hd(k);
@@ -868,18 +872,19 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
   B.thresh = c->thresh; B.part = (double *)dd_part.p; B.cnt = (unsigned long long *)dd_cnt.p;
   B.lists = (uint32_t *)dd_lists.p; B.list_cap = list_cap;
   B.part_dd = (double *)dd_pdd.p; B.cnt_dd = (unsigned long long *)dd_cdd.p;
+  B.dd_tiles = dd_tiles; B.next_tile = (unsigned int *)dd_next.p + 1;
   int occ = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern1, thr1, smem));
   const int grid1 = std::max(1, occ) * c->sms;
-  const int grid2 = std::min<int>(int(n_items), vmb ? L2.blocks : 4 * c->sms);
+  const int grid2 = vmb ? int(std::min<size_t>(n_dd, size_t(L2.blocks))) : std::min<int>(int(n_items), 4 * c->sms);
   // host-side layout of the pinned output block
   double *o_part = (double *)h_out.p;
   double *o_pdd = o_part + 4 * size_t(n_items);
-  unsigned long long *o_cnt = (unsigned long long *)(o_pdd + 4 * size_t(n_items));
+  unsigned long long *o_cnt = (unsigned long long *)(o_pdd + 4 * n_dd);
   unsigned long long *o_cdd = o_cnt + 2 * size_t(n_items);
   auto enqueue_round = [&](cudaStream_t st, bool capturing) -> int {
     CUDA_TRY(cudaMemcpyAsync(dd_items.p, h_items.p, sizeof(BatchItem) * n_items, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemsetAsync(dd_next.p, 0, sizeof(unsigned int), st));
+    CUDA_TRY(cudaMemsetAsync(dd_next.p, 0, 2 * sizeof(unsigned int), st));
     void *args[] = {&B};
     // external event-record nodes when captured, so the kernel can be timed
     // after every replay
@@ -889,9 +894,9 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
     CUDA_TRY(cudaEventRecordWithFlags(c->evk1, st, evflags));
     CUDA_TRY(cudaLaunchKernel(kern2, dim3(grid2), dim3(thr2), args, smem2, st));
     CUDA_TRY(cudaMemcpyAsync(o_part, dd_part.p, sizeof(double) * 4 * n_items, cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaMemcpyAsync(o_pdd, dd_pdd.p, sizeof(double) * 4 * n_items, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(o_pdd, dd_pdd.p, sizeof(double) * 4 * n_dd, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(o_cnt, dd_cnt.p, sizeof(unsigned long long) * 2 * n_items, cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaMemcpyAsync(o_cdd, dd_cdd.p, sizeof(unsigned long long) * 2 * n_items, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(o_cdd, dd_cdd.p, sizeof(unsigned long long) * 2 * n_dd, cudaMemcpyDeviceToHost, st));
     return QED_OK;
   };
   cudaGraphExec_t gexec = nullptr;
@@ -960,11 +965,14 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
       qed_result &q = R[hi[i].diag];
       dd_acc(q.sum_w[0], q.sum_w[1], o_part[4 * i], o_part[4 * i + 1]);
       dd_acc(q.sum_w2[0], q.sum_w2[1], o_part[4 * i + 2], o_part[4 * i + 3]);
-      dd_acc(q.sum_w[0], q.sum_w[1], o_pdd[4 * i], o_pdd[4 * i + 1]);
-      dd_acc(q.sum_w2[0], q.sum_w2[1], o_pdd[4 * i + 2], o_pdd[4 * i + 3]);
+      for (uint32_t kt = 0; kt < dd_tiles; ++kt) {
+        const size_t t = size_t(i) * dd_tiles + kt;
+        dd_acc(q.sum_w[0], q.sum_w[1], o_pdd[4 * t], o_pdd[4 * t + 1]);
+        dd_acc(q.sum_w2[0], q.sum_w2[1], o_pdd[4 * t + 2], o_pdd[4 * t + 3]);
+        q.n_unstable += o_cdd[2 * t + 1];
+      }
       q.n += hi[i].count;
       q.n_flagged += o_cnt[2 * i];
-      q.n_unstable += o_cdd[2 * i + 1];
     }
     // Neyman weights: sigma_g / sqrt(cost_g), cost = FP64 ops per sample with
     // flagged samples counted at the double-double factor

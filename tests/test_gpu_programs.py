@@ -172,3 +172,40 @@ def test_four_loop_batch_deterministic(ctx4):
     d0, r0 = ds[0], r1[0]
     rp = d0.integrate(r0.n, seed=2)
     assert rp.value == pytest.approx(r0.value, rel=1e-9, abs=1e-12)
+
+
+def test_five_loop_points(ctx4):
+    """Five loops (15 lines, 14-dim simplex): Eq. (1) points and densities
+    equal the oracle's sampler on the same Philox counters, and the FP64
+    interpreter's values equal a long-double CPU interpretation of the same
+    program at those points (the programs' generator is pinned against the
+    oracle's integrand at two to four loops)."""
+    from oracle.graphs import deg_table, enumerate_graphs as o_enum
+    from oracle.pdf import f_table, sample_points
+    from oracle.philox import uniforms
+    from paper_1905_08007_b300.five_loop_subset import read
+    from tests.test_programs import interpret, read_programs, _name
+    path = ROOT / "paper_1905_08007_b300" / "csrc" / "_gen" / "vm_n5.bin.z"
+    if not path.exists():
+        pytest.skip("no five-loop programs built")
+    progs = read_programs(path)
+    every = q.enumerate_graphs(5)
+    oall = o_enum(5)
+    for gi in read()[:2]:
+        g = every[gi]
+        d = ctx4.load(g)
+        assert d.n_lines == 15
+        z, f, lp, fl = d.dump_points(3, 6, seed=0)
+        z, f, lp, fl = z.cpu().numpy(), f.cpu().numpy(), lp.cpu().numpy(), fl.cpu().numpy()
+        og = oall[gi]
+        deg = deg_table(og)
+        u = uniforms(np.arange(3, 9, dtype=np.uint64), gi, 0, 2 * 14)
+        x, lpo, _ = sample_points(u, deg, f_table(deg, 15), 15)
+        np.testing.assert_allclose(z, x, rtol=1e-12, atol=0)
+        np.testing.assert_allclose(lp, lpo, rtol=1e-12, atol=1e-12)
+        fc, W = interpret(progs[_name(og)], z, np.longdouble)
+        kappa = (W / np.abs(fc)).astype(float)
+        ok = fl == 0
+        rel = np.abs((f - fc.astype(float)) / fc.astype(float))
+        assert np.all(rel[ok] < 1.5 * TH + 64 * 2.0 ** -64 * kappa[ok]), (gi, rel, kappa)
+

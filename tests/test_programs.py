@@ -5,8 +5,8 @@ numpy interpretation of it reproduces the oracle's subtracted integrand
 are the oracle's, stored by tests/golden/make_four_loop.py at the Eq. (1)
 points of fixed Philox counters.
 
-Instruction (64 bits): lo = A | B << 10 | D << 20 | XA << 30 | ZO << 31,
-hi = SPEC | NOCOMP << 3; operand >= 512 selects a constant.  Unless NOCOMP:
+Instruction (64 bits): lo = A | B << 11 | D << 22, hi = XA | ZO << 1 |
+SPEC << 2 | NOCOMP << 5; operand >= 1024 selects a constant.  Unless NOCOMP:
 X = XA ? A : acc, O = XA ? acc : A, acc = X * B + (ZO ? O : 0); then SPEC
 (1 RCP, 2 ABS, 3 ACCW: W += |A| e(B), 4 END); then D != 0 stores acc."""
 import struct
@@ -25,7 +25,10 @@ GOLDEN4 = ROOT / "tests" / "golden" / "four_loop_points.txt"
 
 def read_programs(path):
     data = path.read_bytes()
-    assert data[:8] == b"QEDVM002"
+    if path.suffix == ".z":
+        import zlib
+        data = zlib.decompress(data)
+    assert data[:8] == b"QEDVM003"
     (count,) = struct.unpack_from("<I", data, 8)
     off = 16
     progs = {}
@@ -57,14 +60,14 @@ def interpret(p, z, dtype=np.float64):
     W = np.zeros(B, dtype=dtype)
 
     def get(x):
-        if x >= 512:
-            return np.full(B, K[x - 512], dtype=dtype), np.full(B, abs(K[x - 512]), dtype=dtype)
+        if x >= 1024:
+            return np.full(B, K[x - 1024], dtype=dtype), np.full(B, abs(K[x - 1024]), dtype=dtype)
         return R[x], E[x]
 
     for w in p["ins"].tolist():
         lo, hi = w & 0xFFFFFFFF, w >> 32
-        a, b, d = lo & 1023, (lo >> 10) & 1023, (lo >> 20) & 1023
-        xa, zo, spec, nocomp = (lo >> 30) & 1, (lo >> 31) & 1, hi & 7, (hi >> 3) & 1
+        a, b, d = lo & 2047, (lo >> 11) & 2047, lo >> 22
+        xa, zo, spec, nocomp = hi & 1, (hi >> 1) & 1, (hi >> 2) & 7, (hi >> 5) & 1
         (va, ea), (vb, eb) = get(a), get(b)
         if not nocomp:
             X, eX = (va, ea) if xa else (acc, ae)
@@ -93,27 +96,33 @@ def _name(g):
 
 
 def _programs(n):
-    path = GEN / f"vm_n{n}.bin"
+    path = GEN / f"vm_n{n}.bin.z"
     if not path.exists():
         pytest.skip(f"{path.name} not built")
     return read_programs(path)
 
 
-@pytest.mark.parametrize("n", [2, 3, 4])
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
 def test_programs_well_formed(n):
     progs = _programs(n)
-    red = [g for g in o_enum(n) if tuple(g.key()) <= tuple(g.mirror().key())]
+    if n == 5:
+        # the five-loop workload: the graphs five_loop_subset.txt lists
+        from paper_1905_08007_b300.five_loop_subset import read
+        every = o_enum(5)
+        red = [every[i] for i in read()]
+    else:
+        red = [g for g in o_enum(n) if tuple(g.key()) <= tuple(g.mirror().key())]
     assert sorted(progs) == sorted(_name(g) for g in red)
     for name, p in progs.items():
-        assert p["n_lines"] == 3 * n and p["n_lines"] <= p["n_regs"] <= 512 and len(p["kon"]) <= 512
+        assert p["n_lines"] == 3 * n and p["n_lines"] <= p["n_regs"] <= 1023 and len(p["kon"]) <= 1024
         ins = p["ins"]
         lo, hi = ins & 0xFFFFFFFF, ins >> 32
-        a, b, d = lo & 1023, (lo >> 10) & 1023, (lo >> 20) & 1023
-        spec = hi & 7
-        assert (hi >> 4).max() == 0 and spec.max() <= 4
+        a, b, d = lo & 2047, (lo >> 11) & 2047, lo >> 22
+        spec = (hi >> 2) & 7
+        assert (hi >> 6).max() == 0 and spec.max() <= 4
         end = int(np.argmax(spec == 4))
         assert spec[end] == 4
-        ok = lambda x: np.where(x >= 512, x - 512 < len(p["kon"]), x < p["n_regs"])   # noqa: E731
+        ok = lambda x: np.where(x >= 1024, x - 1024 < len(p["kon"]), x < p["n_regs"])   # noqa: E731
         assert ok(a[:end + 1]).all() and ok(b[:end + 1]).all(), name
         st = d[:end + 1][d[:end + 1] != 0]
         assert ((st >= p["n_lines"]) & (st < p["n_regs"])).all(), name
