@@ -104,7 +104,7 @@ int qed_ctx_set_launch(qed_ctx *ctx, int threads_per_block, int blocks);
 /* Launch shape of the interpreter kernels (bytecode integrands): threads per
  * block of the FP64 kernels (multiple of 32, 32..256; halved while the
  * shared-memory frame does not fit) and points evaluated per thread by one
- * instruction stream (1 or 2).  Defaults 128 and 2.  Results depend on it
+ * instruction stream (1 or 2).  Defaults 128 and 1.  Results depend on it
  * through the summation order only. */
 int qed_ctx_set_vm(qed_ctx *ctx, int threads_per_block, int points_per_thread);
 /* Relative rounding-error threshold above which a point is re-evaluated in
@@ -132,7 +132,7 @@ int qed_gauge_class(const qed_graph *g, int kmn[3]);
  * 500 GB.  From four loops on, the generator therefore writes each
  * integrand as a program for the library's interpreter kernels instead of
  * source to compile.  data/bytes: the contents of a program file written by
- * the generator (vm_n<n>.bin: "QEDVM003", count, then per program its graph
+ * the generator (vm_n<n>.bin: "QEDVM004", count, then per program its graph
  * name, line count, register count, 64-bit instructions and constants), in
  * host memory, owned by the caller and copied to the device.  Every
  * instruction is checked against its program's register and constant counts

@@ -235,7 +235,7 @@ class Context:
         self.n_programs += cnt.value
         return cnt.value
 
-    def set_vm(self, threads: int = 128, points: int = 2):
+    def set_vm(self, threads: int = 128, points: int = 1):
         """qed_ctx_set_vm: block size and points per thread of the interpreter kernels."""
         _check(load_library().qed_ctx_set_vm(self._h, threads, points))
 

@@ -1124,13 +1124,20 @@ static qvm::Entry gen_vm_graph(const Graph &g, GenStats &st) {
   qvm::Entry e;
   e.name = g.name();
   e.n_lines = g.n_lines();
-  e.prog = C.compile(body.str(), outs);
+  try {
+    e.prog = C.compile(body.str(), outs);
+  } catch (const std::exception &x) {
+    fprintf(stderr, "qed_gen: %s: %s (graph left out)\n", e.name.c_str(), x.what());
+    e.prog.code.clear();
+  }
   return e;
 }
 
 // All graphs of order n, one per mirror pair (the smaller key; QED_VM_ALL=1:
 // both orientations), or the listed ones, on all host threads;
 // QED_VM_LIMIT=k keeps the first k.
+static int vm_failures = 0;
+
 static void gen_vm_order(const std::string &dir, int n, GenStats &st, const std::vector<int> &only) {
   std::vector<Graph> gs;
   const bool all = getenv("QED_VM_ALL") && atoi(getenv("QED_VM_ALL"));
@@ -1174,7 +1181,13 @@ static void gen_vm_order(const std::string &dir, int n, GenStats &st, const std:
     flops += es[i].prog.flops;
     regs = std::max(regs, es[i].prog.n_regs);
   }
-  qvm::write_programs(dir + "/vm_n" + std::to_string(n) + ".bin", es);
+  std::vector<qvm::Entry> good;
+  size_t kon_max = 0;
+  for (auto &e : es)
+    if (!e.prog.code.empty()) { good.push_back(e); kon_max = std::max(kon_max, e.prog.kon.size()); }
+  if (good.size() != es.size()) vm_failures += int(es.size() - good.size());
+  qvm::write_programs(dir + "/vm_n" + std::to_string(n) + ".bin", good);
+  fprintf(stderr, "qed_gen: order %d: at most %zu constants in a program\n", n, kon_max);
   fprintf(stderr, "qed_gen: %zu bytecode programs of order %d, %zu instructions, %.0f FP64 ops, at most %d registers\n",
           es.size(), n, ins, flops, regs);
 }
@@ -1286,7 +1299,7 @@ int main(int argc, char **argv) {
       reg_lines.push_back(g.n_lines());
     }
   }
-  if (reg.empty()) return 0;              // bytecode orders only: the registry is the compiled set's
+  if (reg.empty()) return vm_failures ? 1 : 0;   // bytecode orders only: the registry is the compiled set's
   std::ofstream f(dir + "/qed_registry.h");
   f << "// Generated by qed_gen. Registry of the generated integrands.\n#pragma once\n";
   f << "#define QED_N_GENERATED " << reg.size() << "\n";

@@ -26,16 +26,16 @@
 #include "qed_batch.cuh"
 
 // Instruction (64 bits, written by the generator's fuse step):
-//   lo = A | B << 11 | D << 22,  hi = XA | ZO << 1 | SPEC << 2 | NOCOMP << 5
+//   lo = A | B << 13,  hi = XA | ZO << 1 | SPEC << 2 | NOCOMP << 5 | D << 6
 //   1. unless NOCOMP:  X = XA ? A : acc,  O = XA ? acc : A,
 //                      acc = X * B + (ZO ? O : 0)          (e lane alike)
 //   2. SPEC 1: acc = 1 / acc, e = |acc|;  2: e = |acc|;  3: W += |A.v| * B.e;
 //      4: end
 //   3. store acc in R[D] (D = 0: in the spare register)
-// Operands A, B: a register index, or 1024 + a constant index.  Every
+// Operands A, B: a register index, or 4096 + a constant index.  Every
 // instruction reads both operands (the generator names the constants 0 or 1
 // where one is unused), so the common path has no branch on the operation.
-#define VM_KFLAG 1024u
+#define VM_KFLAG 4096u
 #define VM_SP_RCP 1u
 #define VM_SP_ABS 2u
 #define VM_SP_ACCW 3u
@@ -99,57 +99,58 @@ template <> struct VmVec<float, 2> {
   }
 };
 
-// Shared-memory frame of a block: the constants (value and magnitude, each
-// repeated P times), then the register files, value lanes then e lanes, of
-// n_regs + 1 registers (the last takes the stores of instructions without a
-// target), register r of point p of thread t at ((r * T) + t) * P + p.
+// Shared-memory frame of a block: a value region (the constants, each
+// repeated P times, then the register files of n_regs + 1 registers, the
+// last taking the stores of instructions without a target; register r of
+// point p of thread t at ((r * T) + t) * P + p), then an e region laid out
+// the same way at half the size (e is half as wide as the value in both
+// frames), so that an e address is X + (value address) / 2.
+template <class R, int P>
+__host__ __device__ __forceinline__ size_t vm_value_bytes(int n_kon, int n_regs, int T) {
+  return (size_t(n_kon) * P * sizeof(R) + size_t(n_regs + 1) * T * P * sizeof(R) + 15) & ~size_t(15);
+}
 template <class R, int P>
 __host__ __device__ __forceinline__ size_t vm_smem_bytes(int n_kon, int n_regs, int T) {
-  typedef typename VmE<R>::T E;
-  const size_t k = (size_t(n_kon) * P * (sizeof(R) + sizeof(E)) + 15) & ~size_t(15);
-  return k + size_t(n_regs + 1) * T * P * (sizeof(R) + sizeof(E));
+  static_assert(2 * sizeof(typename VmE<R>::T) == sizeof(R), "e lane is half the value width");
+  const size_t v = vm_value_bytes<R, P>(n_kon, n_regs, T);
+  return v + v / 2;
 }
 
 template <class R, int P>
 struct VmFrame {
   typedef typename VmE<R>::T E;
   unsigned char *sm;
-  uint32_t kv, ke;          // byte offsets of the constant tables
-  uint32_t vt, et;          // this thread's register 0 (value, e lane)
-  uint32_t vs, es;          // bytes from one register to the next
+  uint32_t ex;              // start of the e region
+  uint32_t vt;              // this thread's register 0 (value lane)
+  uint32_t vs;              // bytes from one register to the next
   uint32_t spare;
   __device__ __forceinline__ void setup(const VmCode &C, unsigned char *smem) {
     sm = smem;
     const int T = blockDim.x;
-    kv = 0;
-    ke = uint32_t(C.n_kon) * P * sizeof(R);
+    ex = uint32_t(vm_value_bytes<R, P>(C.n_kon, C.n_regs, T));
     R *k = reinterpret_cast<R *>(smem);
-    E *kabs = reinterpret_cast<E *>(smem + ke);
+    E *kabs = reinterpret_cast<E *>(smem + ex);
     for (int i = threadIdx.x; i < C.n_kon * P; i += blockDim.x) {
       const double c = C.kon[i / P];
       k[i] = R(c);
       kabs[i] = E(fabs(c));
     }
-    const uint32_t v0 = uint32_t((size_t(C.n_kon) * P * (sizeof(R) + sizeof(E)) + 15) & ~size_t(15));
-    const uint32_t e0 = v0 + uint32_t(C.n_regs + 1) * T * P * sizeof(R);
+    const uint32_t v0 = uint32_t(C.n_kon) * P * sizeof(R);
     vs = uint32_t(T) * P * sizeof(R);
-    es = uint32_t(T) * P * sizeof(E);
     vt = v0 + threadIdx.x * P * sizeof(R);
-    et = e0 + threadIdx.x * P * sizeof(E);
     spare = uint32_t(C.n_regs);
     __syncthreads();
   }
   __device__ __forceinline__ void put(uint32_t r, const R (&v)[P], const E (&e)[P]) {
-    VmVec<R, P>::st(sm + vt + r * vs, v);
-    VmVec<E, P>::st(sm + et + r * es, e);
+    const uint32_t vo = vt + r * vs;
+    VmVec<R, P>::st(sm + vo, v);
+    VmVec<E, P>::st(sm + ex + (vo >> 1), e);
   }
   __device__ __forceinline__ void get(uint32_t a, R (&v)[P], E (&e)[P]) const {
-    const bool k = a >= VM_KFLAG;
     const uint32_t i = a & (VM_KFLAG - 1u);
-    const uint32_t vo = k ? kv + i * uint32_t(P * sizeof(R)) : vt + a * vs;
-    const uint32_t eo = k ? ke + i * uint32_t(P * sizeof(E)) : et + a * es;
+    const uint32_t vo = a >= VM_KFLAG ? i * uint32_t(P * sizeof(R)) : vt + a * vs;
     VmVec<R, P>::ld(sm + vo, v);
-    VmVec<E, P>::ld(sm + eo, e);
+    VmVec<E, P>::ld(sm + ex + (vo >> 1), e);
   }
 
   // One instruction whose operands are already loaded: compute, special,
@@ -157,6 +158,24 @@ struct VmFrame {
   __device__ __forceinline__ bool step(uint32_t lo, uint32_t hi, const R (&va)[P], const E (&ea)[P],
                                        const R (&vb)[P], const E (&eb)[P], R (&acc)[P], E (&ae)[P],
                                        double (&W)[P]) {
+    if (!(hi & (VM_NOCOMP | (7u << 2)))) {        // the common case: compute and store
+      const bool xa = hi & 1u, zo = (hi >> 1) & 1u;
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const R X = xa ? va[p] : acc[p], O = xa ? acc[p] : va[p];
+        const E eX = xa ? ea[p] : ae[p], eO = xa ? ae[p] : ea[p];
+        acc[p] = vm_fma(X, vb[p], zo ? O : R(0.0));
+        ae[p] = eX * eb[p] + (zo ? eO : E(0));
+      }
+      const uint32_t d = hi >> 6;
+      put(d ? d : spare, acc, ae);
+      return false;
+    }
+    return step_slow(lo, hi, va, ea, vb, eb, acc, ae, W);
+  }
+  __device__ __forceinline__ bool step_slow(uint32_t lo, uint32_t hi, const R (&va)[P], const E (&ea)[P],
+                                         const R (&vb)[P], const E (&eb)[P], R (&acc)[P], E (&ae)[P],
+                                         double (&W)[P]) {
     if (!(hi & VM_NOCOMP)) {
       const bool xa = hi & 1u, zo = (hi >> 1) & 1u;
 #pragma unroll
@@ -185,7 +204,7 @@ struct VmFrame {
         }
       }
     }
-    const uint32_t d = lo >> 22;
+    const uint32_t d = hi >> 6;
     put(d ? d : spare, acc, ae);
     return false;
   }
@@ -196,9 +215,10 @@ struct VmFrame {
   // instruction are loaded before this one computes and stores (the
   // generator never lets an instruction read the register the previous one
   // writes), so shared-memory latency is off the chain through acc; the
-  // instruction stream is loaded four 16-byte groups (eight instructions)
-  // ahead.  The host pads every program with zero words to an even count
-  // plus four zero groups, so every look-ahead stays inside the program.
+  // instruction stream is loaded in blocks of four 16-byte groups (eight
+  // instructions), one block ahead.  The host pads every program with zero
+  // words to an even count plus eight zero groups, so every look-ahead
+  // stays inside the program.
   template <int N>
   __device__ __forceinline__ void eval(const VmCode &C, const R (&z)[P][N], R (&f)[P], double (&absum)[P]) {
 #pragma unroll
@@ -215,22 +235,33 @@ struct VmFrame {
 #pragma unroll
     for (int p = 0; p < P; ++p) { acc[p] = R(0.0); ae[p] = E(0); W[p] = 0.0; }
     const uint4 *ip = reinterpret_cast<const uint4 *>(C.ins);
-    uint4 g0 = __ldg(ip), g1 = __ldg(ip + 1), g2 = __ldg(ip + 2), g3 = __ldg(ip + 3);
+    uint4 g[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) g[j] = __ldg(ip + j);
     R va[P], vb[P], na[P], nb[P];
     E ea[P], eb[P], nea[P], neb[P];
-    get(g0.x & 2047u, va, ea);
-    get((g0.x >> 11) & 2047u, vb, eb);
-    for (;; ++ip) {
-      get(g0.z & 2047u, na, nea);
-      get((g0.z >> 11) & 2047u, nb, neb);
-      if (step(g0.x, g0.y, va, ea, vb, eb, acc, ae, W)) break;
-      get(g1.x & 2047u, va, ea);
-      get((g1.x >> 11) & 2047u, vb, eb);
-      if (step(g0.z, g0.w, na, nea, nb, neb, acc, ae, W)) break;
-      g0 = g1;
-      g1 = g2;
-      g2 = g3;
-      g3 = __ldg(ip + 4);
+    get(g[0].x & 8191u, va, ea);
+    get((g[0].x >> 13) & 8191u, vb, eb);
+    for (;; ip += 4) {
+      uint4 h[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) h[j] = __ldg(ip + 4 + j);
+      bool done = false;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        // slot 2j: (g[j].x, g[j].y), next operands (g[j].z)
+        get(g[j].z & 8191u, na, nea);
+        get((g[j].z >> 13) & 8191u, nb, neb);
+        if (step(g[j].x, g[j].y, va, ea, vb, eb, acc, ae, W)) { done = true; break; }
+        // slot 2j+1: (g[j].z, g[j].w), next operands: the following group's x
+        const uint32_t nx = j < 3 ? g[j + 1].x : h[0].x;
+        get(nx & 8191u, va, ea);
+        get((nx >> 13) & 8191u, vb, eb);
+        if (step(g[j].z, g[j].w, na, nea, nb, neb, acc, ae, W)) { done = true; break; }
+      }
+      if (done) break;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) g[j] = h[j];
     }
 #pragma unroll
     for (int p = 0; p < P; ++p) { f[p] = acc[p]; absum[p] = W[p]; }

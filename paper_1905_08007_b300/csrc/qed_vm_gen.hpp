@@ -13,7 +13,7 @@
 //   register file R[0..n_regs) of (v, e) pairs (z[0..N) preloaded in
 //   R[0..N) with e = z), and a double W that collects the monomial
 //   absolute sum of the integrand;
-//   per program: a table K of constants (operand flag 1024 selects K, with
+//   per program: a table K of constants (operand flag 4096 selects K, with
 //   e = |K|).
 //   The e lane follows the value lane through +, *, fma with the operands'
 //   e values; for the quantities whose magnitude the compiled path takes as
@@ -35,10 +35,10 @@
 //   ST a        R[a] = acc
 //   ACCW a b    W += |a.v| * b.e
 //   LDMUL a b   acc = a * b
-// (operands: a register index, or 1024 + a constant index), and fuses them
+// (operands: a register index, or 4096 + a constant index), and fuses them
 // into 64-bit instructions that the interpreter executes without a dispatch
 // on the operation:
-//   lo = A | B << 11 | D << 22,  hi = XA | ZO << 1 | SPEC << 2 | NOCOMP << 5
+//   lo = A | B << 13,  hi = XA | ZO << 1 | SPEC << 2 | NOCOMP << 5 | D << 6
 //   1. unless NOCOMP:  X = XA ? A : acc,  O = XA ? acc : A,
 //                      acc = X * B + (ZO ? O : 0)           (e lane alike)
 //   2. SPEC 1 RCP: acc = 1 / acc, e = |acc|;  2 ABS: e = |acc|;
@@ -59,6 +59,7 @@
 #include <cstring>
 #include <map>
 #include <set>
+#include <stdexcept>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -66,20 +67,21 @@
 namespace qvm {
 
 enum Op : uint32_t { END = 0, LD, ADD, MUL, FMA, FMAC, RCP, ABS, ST, ACCW, LDMUL };
-constexpr int KFLAG = 1024;         // operand >= KFLAG: constant K[operand - KFLAG]
+constexpr int KFLAG = 4096;         // operand >= KFLAG: constant K[operand - KFLAG]
 constexpr int MAX_REGS = 1023;
-constexpr int MAX_KON = 1024;
+constexpr int MAX_KON = 4096;
 
+// micro-operation word: op[0:4) a[4:17) b[17:30)
 inline uint32_t enc(Op op, int a = 0, int b = 0) {
-  return uint32_t(op) | (uint32_t(a) << 4) | (uint32_t(b) << 15);
+  return uint32_t(op) | (uint32_t(a) << 4) | (uint32_t(b) << 17);
 }
 
 enum : uint32_t { SP_NONE = 0, SP_RCP = 1, SP_ABS = 2, SP_ACCW = 3, SP_END = 4 };
 constexpr uint32_t NOCOMP = 32u;
 
 inline uint64_t word(int A, int B, int D, bool xa, bool zo, uint32_t spec, bool nocomp) {
-  const uint32_t lo = uint32_t(A) | (uint32_t(B) << 11) | (uint32_t(D) << 22);
-  const uint32_t hi = uint32_t(xa) | (uint32_t(zo) << 1) | (spec << 2) | (nocomp ? NOCOMP : 0u);
+  const uint32_t lo = uint32_t(A) | (uint32_t(B) << 13);
+  const uint32_t hi = uint32_t(xa) | (uint32_t(zo) << 1) | (spec << 2) | (nocomp ? NOCOMP : 0u) | (uint32_t(D) << 6);
   return uint64_t(lo) | (uint64_t(hi) << 32);
 }
 
@@ -379,8 +381,7 @@ class Compiler {
   int alloc() {
     for (int r = N; r < MAX_REGS; ++r)
       if (!used[r]) { used[r] = true; if (r + 1 > hi) hi = r + 1; return r; }
-    fprintf(stderr, "vm: out of registers\n");
-    exit(1);
+    throw std::runtime_error("out of registers");
   }
   void free_reg(int r) { if (r >= N) used[r] = false; }
   void release(const std::string &n) {
@@ -398,7 +399,7 @@ class Compiler {
     bool open = false;          // last instruction can still take a special / store
     bool has_spec = false, has_st = false;
     for (uint32_t w : P.ins) {
-      const int op = int(w & 15u), a = int((w >> 4) & 2047u), b = int((w >> 15) & 2047u);
+      const int op = int(w & 15u), a = int((w >> 4) & 8191u), b = int((w >> 17) & 8191u);
       auto put = [&](uint64_t x, bool can_extend) {
         C.push_back(x);
         open = can_extend;
@@ -420,7 +421,7 @@ class Compiler {
           break;
         }
         case ST:
-          if (open && !has_st) { C.back() |= uint64_t(uint32_t(a)) << 22; has_st = true; }
+          if (open && !has_st) { C.back() |= uint64_t(uint32_t(a)) << (32 + 6); has_st = true; }
           else { put(word(zero, one, a, false, false, SP_NONE, true), false); }
           break;
         case ACCW: put(word(a, b, 0, false, false, SP_ACCW, true), false); break;
@@ -433,8 +434,8 @@ class Compiler {
     out.reserve(C.size() + C.size() / 8);
     for (size_t i = 0; i < C.size(); ++i) {
       if (i > 0) {
-        const uint32_t d = uint32_t(C[i - 1] >> 22) & 1023u;
-        const uint32_t a = uint32_t(C[i]) & 2047u, b = uint32_t(C[i] >> 11) & 2047u;
+        const uint32_t d = uint32_t(C[i - 1] >> (32 + 6)) & 1023u;
+        const uint32_t a = uint32_t(C[i]) & 8191u, b = uint32_t(C[i] >> 13) & 8191u;
         if (d != 0 && (a == d || b == d)) out.push_back(word(zero, one, 0, false, false, SP_NONE, true));
       }
       out.push_back(C[i]);
@@ -445,7 +446,7 @@ class Compiler {
   int kon(double c) {
     auto it = kidx.find(c);
     if (it != kidx.end()) return KFLAG + it->second;
-    if (int(P.kon.size()) >= MAX_KON) { fprintf(stderr, "vm: too many constants\n"); exit(1); }
+    if (int(P.kon.size()) >= MAX_KON) throw std::runtime_error("more than 4096 constants");
     kidx[c] = int(P.kon.size());
     P.kon.push_back(c);
     return KFLAG + int(P.kon.size()) - 1;
@@ -583,7 +584,7 @@ class Compiler {
 // ---------------------------------------------------------------------------
 // program file
 // ---------------------------------------------------------------------------
-// Layout (little endian): "QEDVM003", u32 count, u32 0, then per program a
+// Layout (little endian): "QEDVM004", u32 count, u32 0, then per program a
 // 64-byte name, i32 n_lines, n_regs, n_ins, n_kon, f64 flops, the n_ins
 // 64-bit instructions and the constants.
 struct Entry {
@@ -595,7 +596,7 @@ struct Entry {
 inline void write_programs(const std::string &path, const std::vector<Entry> &es) {
   FILE *f = fopen(path.c_str(), "wb");
   if (!f) { fprintf(stderr, "vm: cannot write %s\n", path.c_str()); exit(1); }
-  fwrite("QEDVM003", 1, 8, f);
+  fwrite("QEDVM004", 1, 8, f);
   const uint32_t hdr[2] = {uint32_t(es.size()), 0u};
   fwrite(hdr, 4, 2, f);
   for (auto &e : es) {

@@ -90,7 +90,7 @@ struct qed_ctx {
   std::vector<void *> vm_bufs;
   bool prefer_vm = false;
   int vm_threads = 128;      // threads per block of the FP64 interpreter kernels
-  int vm_points = 2;         // points per thread of the FP64 interpreter kernels
+  int vm_points = 1;         // points per thread of the FP64 interpreter kernels
 };
 
 struct qed_diag {
@@ -247,19 +247,19 @@ extern "C" int qed_ctx_set_threshold(qed_ctx *c, double rel) {
 // counts here, so that the interpreter's shared-memory accesses stay inside
 // the frame the host sized for it.
 static bool vm_check(const uint2 *ins, int n_ins, int n_regs, int n_kon, int n_lines, std::string &why) {
-  if (n_regs < n_lines || n_regs > 1023 || n_kon < 0 || n_kon > 1024 || n_ins < 1) { why = "program sizes out of range"; return false; }
+  if (n_regs < n_lines || n_regs > 1023 || n_kon < 0 || n_kon > 4096 || n_ins < 1) { why = "program sizes out of range"; return false; }
   auto ok = [&](uint32_t a) { return a < VM_KFLAG ? int(a) < n_regs : int(a - VM_KFLAG) < n_kon; };
   for (int i = 0; i < n_ins; ++i) {
     const uint32_t lo = ins[i].x, hi = ins[i].y;
-    const uint32_t a = lo & 2047u, b = (lo >> 11) & 2047u, d = lo >> 22, sp = (hi >> 2) & 7u;
-    if ((hi >> 6) || sp > VM_SP_END) { why = "bad special field"; return false; }
+    const uint32_t a = lo & 8191u, b = (lo >> 13) & 8191u, d = (hi >> 6) & 1023u, sp = (hi >> 2) & 7u;
+    if ((lo >> 26) || (hi >> 16) || sp > VM_SP_END) { why = "reserved or bad instruction field"; return false; }
     // both operands are read by every instruction
     if (!ok(a) || !ok(b)) { why = "operand out of range"; return false; }
     if (d != 0 && (int(d) < n_lines || int(d) >= n_regs)) { why = "store target out of range"; return false; }
     // the interpreter loads an instruction's operands before the previous
     // instruction stores
     if (i > 0) {
-      const uint32_t pd = ins[i - 1].x >> 22;
+      const uint32_t pd = (ins[i - 1].y >> 6) & 1023u;
       if (pd != 0 && (a == pd || b == pd)) { why = "instruction reads the register the previous one writes"; return false; }
     }
     if (sp == VM_SP_END) {
@@ -274,7 +274,7 @@ static bool vm_check(const uint2 *ins, int n_ins, int n_regs, int n_kon, int n_l
 extern "C" int qed_programs_load(qed_ctx *c, const void *data, size_t bytes, int *count) {
   if (!c || !data) return set_err(QED_EINVAL, "ctx/data is NULL");
   const unsigned char *p = static_cast<const unsigned char *>(data), *end = p + bytes;
-  if (bytes < 16 || std::memcmp(p, "QEDVM003", 8) != 0) return set_err(QED_EINVAL, "not a qed program file");
+  if (bytes < 16 || std::memcmp(p, "QEDVM004", 8) != 0) return set_err(QED_EINVAL, "not a qed program file");
   uint32_t n = 0;
   std::memcpy(&n, p + 8, 4);
   p += 16;
@@ -302,13 +302,13 @@ extern "C" int qed_programs_load(qed_ctx *c, const void *data, size_t bytes, int
     std::memcpy(tmp.data(), r.ins, ib);
     if (!vm_check(tmp.data(), m[2], m[1], m[3], m[0], why)) return set_err(QED_EINVAL, "program " + r.pr.name + ": " + why);
     p += ib + kb;
-    words += (((size_t(m[2]) + 1) & ~size_t(1)) + 8) * 2;  // 32-bit words: pairs, plus 4 zero groups
+    words += (((size_t(m[2]) + 1) & ~size_t(1)) + 16) * 2;  // 32-bit words: pairs, plus 8 zero groups
     kons += size_t(m[3]);
     recs.push_back(r);
   }
   CUDA_TRY(cudaSetDevice(c->device));
   // one buffer per file: instructions (each program padded with zero words
-  // to an even count, so 16-byte aligned, then four zero groups that the
+  // to an even count, so 16-byte aligned, then eight zero groups that the
   // interpreter's look-ahead reads but never executes: END comes first and
   // a zero word names register 0), then the constants
   void *buf = nullptr;
@@ -320,7 +320,7 @@ extern "C" int qed_programs_load(qed_ctx *c, const void *data, size_t bytes, int
   for (auto &r : recs) {
     std::memcpy(host.data() + wo, r.ins, size_t(r.pr.n_ins) * 8);
     r.pr.d_ins = reinterpret_cast<const uint2 *>(static_cast<unsigned char *>(buf) + wo);
-    wo += (((size_t(r.pr.n_ins) + 1) & ~size_t(1)) + 8) * 8;
+    wo += (((size_t(r.pr.n_ins) + 1) & ~size_t(1)) + 16) * 8;
     std::memcpy(host.data() + ko, r.kon, size_t(r.pr.n_kon) * 8);
     r.pr.d_kon = reinterpret_cast<const double *>(static_cast<unsigned char *>(buf) + ko);
     ko += size_t(r.pr.n_kon) * 8;

@@ -5,8 +5,8 @@ numpy interpretation of it reproduces the oracle's subtracted integrand
 are the oracle's, stored by tests/golden/make_four_loop.py at the Eq. (1)
 points of fixed Philox counters.
 
-Instruction (64 bits): lo = A | B << 11 | D << 22, hi = XA | ZO << 1 |
-SPEC << 2 | NOCOMP << 5; operand >= 1024 selects a constant.  Unless NOCOMP:
+Instruction (64 bits): lo = A | B << 13, hi = XA | ZO << 1 | SPEC << 2 |
+NOCOMP << 5 | D << 6; operand >= 4096 selects a constant.  Unless NOCOMP:
 X = XA ? A : acc, O = XA ? acc : A, acc = X * B + (ZO ? O : 0); then SPEC
 (1 RCP, 2 ABS, 3 ACCW: W += |A| e(B), 4 END); then D != 0 stores acc."""
 import struct
@@ -28,7 +28,7 @@ def read_programs(path):
     if path.suffix == ".z":
         import zlib
         data = zlib.decompress(data)
-    assert data[:8] == b"QEDVM003"
+    assert data[:8] == b"QEDVM004"
     (count,) = struct.unpack_from("<I", data, 8)
     off = 16
     progs = {}
@@ -60,13 +60,13 @@ def interpret(p, z, dtype=np.float64):
     W = np.zeros(B, dtype=dtype)
 
     def get(x):
-        if x >= 1024:
-            return np.full(B, K[x - 1024], dtype=dtype), np.full(B, abs(K[x - 1024]), dtype=dtype)
+        if x >= 4096:
+            return np.full(B, K[x - 4096], dtype=dtype), np.full(B, abs(K[x - 4096]), dtype=dtype)
         return R[x], E[x]
 
     for w in p["ins"].tolist():
         lo, hi = w & 0xFFFFFFFF, w >> 32
-        a, b, d = lo & 2047, (lo >> 11) & 2047, lo >> 22
+        a, b, d = lo & 8191, (lo >> 13) & 8191, (hi >> 6) & 1023
         xa, zo, spec, nocomp = hi & 1, (hi >> 1) & 1, (hi >> 2) & 7, (hi >> 5) & 1
         (va, ea), (vb, eb) = get(a), get(b)
         if not nocomp:
@@ -114,15 +114,15 @@ def test_programs_well_formed(n):
         red = [g for g in o_enum(n) if tuple(g.key()) <= tuple(g.mirror().key())]
     assert sorted(progs) == sorted(_name(g) for g in red)
     for name, p in progs.items():
-        assert p["n_lines"] == 3 * n and p["n_lines"] <= p["n_regs"] <= 1023 and len(p["kon"]) <= 1024
+        assert p["n_lines"] == 3 * n and p["n_lines"] <= p["n_regs"] <= 1023 and len(p["kon"]) <= 4096
         ins = p["ins"]
         lo, hi = ins & 0xFFFFFFFF, ins >> 32
-        a, b, d = lo & 2047, (lo >> 11) & 2047, lo >> 22
+        a, b, d = lo & 8191, (lo >> 13) & 8191, (hi >> 6) & 1023
         spec = (hi >> 2) & 7
-        assert (hi >> 6).max() == 0 and spec.max() <= 4
+        assert (lo >> 26).max() == 0 and (hi >> 16).max() == 0 and spec.max() <= 4
         end = int(np.argmax(spec == 4))
         assert spec[end] == 4
-        ok = lambda x: np.where(x >= 1024, x - 1024 < len(p["kon"]), x < p["n_regs"])   # noqa: E731
+        ok = lambda x: np.where(x >= 4096, x - 4096 < len(p["kon"]), x < p["n_regs"])   # noqa: E731
         assert ok(a[:end + 1]).all() and ok(b[:end + 1]).all(), name
         st = d[:end + 1][d[:end + 1] != 0]
         assert ((st >= p["n_lines"]) & (st < p["n_regs"])).all(), name
