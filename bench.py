@@ -47,8 +47,9 @@ SIGMA_TARGETS = {1: 1e-5, 2: 1e-5, 3: 1e-4, 4: 5e-3, 5: 0.1}
 # three-loop set (BASELINE's config 3 budget)
 DEFAULT_SAMPLES = {1: 1e8, 2: 1e8, 3: 2e7, 4: 2 ** 16, 5: 2 ** 12}
 # work-item size of the batched kernel per order (a four-loop sample is ~1e5
-# FP64 operations, a five-loop one ~1e6)
-CHUNK = {1: 1 << 18, 2: 1 << 18, 3: 1 << 18, 4: 1 << 13, 5: 1 << 11}
+# FP64 operations, a five-loop one ~1e6): at four loops 2048 samples give
+# about 15 items per persistent block and round, so the blocks finish together
+CHUNK = {1: 1 << 18, 2: 1 << 18, 3: 1 << 18, 4: 1 << 11, 5: 1 << 11}
 CLOSED_FORM = {1: 0.5, 2: TWO_LOOP_TARGET}
 
 
@@ -262,7 +263,7 @@ def run_native(args):
             tune(d, steps=ts, n=tn, lr=0.08, seed=args.seed + 7)
     setup_s = time.perf_counter() - t0
     flops = [d.flops_per_sample() for d in diags]
-    rounds, chunk = 4, CHUNK[args.order]
+    rounds, chunk = 4, int(args.chunk or CHUNK[args.order])
 
     def step(s):
         base = (s * ws + rank) * total + (1 << 40)      # fresh counters every step and rank
@@ -333,10 +334,11 @@ def run_native(args):
         "config": {"workload": f"{args.order}-loop lepton-loop-free vertex set: {len(graphs)} graphs"
                                + {4: " (one per mirror pair, bytecode integrands)",
                                   5: " (the 64-graph workload, bytecode integrands)"}.get(args.order, "") + ", "
-                               f"{total:.0e} Philox samples per step shared by running variance, Deg "
-                               "calibrated + gradient-tuned densities, forest-subtracted FP64 integrand, "
-                               "double-double re-evaluation, persistent batched kernel (4 CUDA-graph "
-                               "rounds per step)",
+                               f"{total:.0e} Philox samples per step shared by running variance, "
+                               + {4: "gradient-tuned Deg-rule densities", 5: "Deg-rule densities"}.get(
+                                   args.order, "Deg-calibrated + gradient-tuned densities")
+                               + ", forest-subtracted FP64 integrand, double-double re-evaluation, "
+                               "persistent batched kernel (4 CUDA-graph rounds per step)",
                    "loops": args.order, "graphs": len(graphs), "samples_per_step": total, "seed": args.seed, "l2_flush": True,
                    "launch": {"threads": 256, "items_per_round": n_items, "chunk": chunk},
                    "setup_seconds_calibrate_and_tune": setup_s},
@@ -382,6 +384,7 @@ def main(argv=None):
     ap.add_argument("--samples", type=float, default=None, help="samples per graph per step")
     ap.add_argument("--order", type=int, default=2, choices=[1, 2, 3, 4, 5], help="loop order of the graph set")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=None, help="samples per work item of the batched kernel")
     ap.add_argument("--ref-samples", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", dest="compare", action="store_false",

@@ -61,7 +61,40 @@ template <> struct VmE<dd> { typedef double T; };
 __device__ __forceinline__ double vm_mag(double x) { return fabs(x); }
 __device__ __forceinline__ double vm_mag(dd x) { return fabs(x.hi + x.lo); }
 __device__ __forceinline__ double vm_fma(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ dd vm_fma(dd a, dd b, dd c) { return a * b + c; }
+// a * b + c in double-double, the one arithmetic step of the interpreter.
+// General case: the exact product of the high parts (two-product), the
+// cross terms a.hi b.lo + a.lo b.hi added to its low part (a.lo b.lo, below
+// 2^-106 |a b|, dropped), one two-sum of the high parts, every low part
+// folded into the sum's error term, one renormalisation: 15 FP64 operations
+// instead of the 27 of a double-double product followed by a full
+// double-double sum.  Its error is a few 2^-106 (|a b| + |c|), bounded by
+// the operands' magnitudes rather than the result's -- the form the
+// absolute-value lane sums up for the rounding-error estimate, so that
+// estimate stays a bound under cancellation between forest terms.
+// Two operand patterns skip work (tested on bit patterns, with integer
+// compares; both are warp-uniform when the operand is a constant or the
+// instruction has no addend, and give the same value as the general case
+// would up to its rounding): c = 0 (loads and products, about 40 % of the
+// instructions of a four-loop program) leaves the product alone, 7
+// operations; b = 1 (moves and sums, about 20 %) leaves the sum alone, 11
+// operations, or none for a move.
+__device__ __forceinline__ bool vm_bits_zero(dd x) {
+  return ((__double_as_longlong(x.hi) | __double_as_longlong(x.lo)) << 1) == 0;
+}
+__device__ __forceinline__ dd vm_fma(dd a, dd b, dd c) {
+  if (__double_as_longlong(b.hi) == 0x3ff0000000000000ll && __double_as_longlong(b.lo) == 0) {
+    if (vm_bits_zero(c)) return a;
+    const dd s = two_sum(a.hi, c.hi);
+    return quick_two_sum(s.hi, __dadd_rn(__dadd_rn(s.lo, a.lo), c.lo));
+  }
+  const double p = __dmul_rn(a.hi, b.hi);
+  double pl = __fma_rn(a.hi, b.hi, -p);
+  pl = __fma_rn(a.hi, b.lo, pl);
+  pl = __fma_rn(a.lo, b.hi, pl);
+  if (vm_bits_zero(c)) return quick_two_sum(p, pl);
+  const dd s = two_sum(p, c.hi);
+  return quick_two_sum(s.hi, __dadd_rn(__dadd_rn(s.lo, pl), c.lo));
+}
 __device__ __forceinline__ double vm_rcp(double a) { return 1.0 / a; }
 __device__ __forceinline__ dd vm_rcp(dd a) { return dd(1.0) / a; }
 template <class E> __device__ __forceinline__ E vm_abs_e(double m);

@@ -67,10 +67,19 @@ def test_programs_match_compiled_points(ctxs, n, idx):
         assert ok.mean() > 0.5
         rel = np.abs(fv - fc)[ok] / np.abs(fc[ok])
         assert rel.max() < 2.5 * TH, rel.max()
-        # double-double at the same points
+        # double-double at the same points: the interpreter's fused
+        # multiply-add and the compiled code's product-then-sum round
+        # differently, by a few 2^-106 times the sum of the magnitudes
+        # involved, like the FP64 error at the same point with 2^-53 in
+        # place of 2^-106.  So they agree to 1e-13 relative, or at points
+        # where the forest terms cancel beyond ~1e20 (the FP64 value's own
+        # error then exceeds 1e4) to within 2^-43 of that FP64 error.
         gc = dc.eval_points(zc, prec=1).cpu().numpy()
         gv = dv.eval_points(zc, prec=1).cpu().numpy()
-        assert np.max(np.abs(gv - gc) / np.abs(gc)) < 1e-13
+        ddiff = np.abs(gv - gc)
+        assert np.all(ddiff[ok] <= 1e-13 * np.abs(gc[ok]))
+        bound = 1e-13 * np.abs(gc) + 2.0 ** -43 * np.abs(fc - gc)
+        assert np.all(ddiff <= bound), np.max(ddiff / bound)
         # FP64 evaluation at caller points equals the dump's values
         ev = dv.eval_points(zc, prec=0).cpu().numpy()
         np.testing.assert_array_equal(ev, fv)
