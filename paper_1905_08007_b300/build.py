@@ -12,7 +12,8 @@ Steps:
    to this file;
 3. run the generator's bytecode back end for the program orders: it writes
    ``csrc/_gen/vm_n<n>.bin`` (one program per mirror-reduced graph; at five
-   loops the 64 graphs of ``five_loop_subset.txt``), stored zlib-compressed as
+   loops the 64 graphs of ``five_loop_subset.txt``, built only when asked
+   for with ``--programs 2 3 4 5``), stored zlib-compressed as
    ``vm_n<n>.bin.z``; the library's interpreter kernels evaluate them (four
    loops and up have no compiled integrands; the lower orders are there to
    compare the two paths).
@@ -38,7 +39,9 @@ INCLUDE = ROOT / "include"
 BUILD = ROOT / "_build"
 LIB = PKG / "libqedmc.so"
 DEFAULT_ORDERS = (1, 2, 3)
-DEFAULT_PROGRAM_ORDERS = (2, 3, 4, 5)      # 5: the 64-graph workload of five_loop_subset.txt
+# five loops (the 64-graph workload of five_loop_subset.txt, more than an
+# hour of generation on 8 cores) only on request: --programs 2 3 4 5
+DEFAULT_PROGRAM_ORDERS = (2, 3, 4)
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -74,25 +77,35 @@ def _generator():
     return gen_bin
 
 
+def _program_key(n):
+    deps = GEN_SRC + ([PKG / "five_loop_subset.txt"] if n == 5 else [])
+    return _digest(deps, extra=f"programs order {n}")
+
+
 def build_programs(orders=DEFAULT_PROGRAM_ORDERS, force=False):
-    """Bytecode programs vm_n<n>.bin for the interpreter kernels."""
+    """Bytecode programs vm_n<n>.bin.z for the interpreter kernels, one file
+    and one stamp per loop order: an order is generated again only when its
+    file is missing or the generator (or, at five loops, the graph list)
+    changed, and the files of other orders are left alone."""
     orders = tuple(int(o) for o in orders)
     BUILD.mkdir(exist_ok=True)
     GEN.mkdir(exist_ok=True)
-    outs = [GEN / f"vm_n{n}.bin.z" for n in orders]
-    stamp = BUILD / "programs.stamp"
-    key = _digest(GEN_SRC + [PKG / "five_loop_subset.txt"], extra=repr(orders))
-    if not force and all(o.exists() for o in outs) and stamp.exists() and stamp.read_text() == key:
-        return outs
-    for old in list(GEN.glob("vm_n*.bin")) + list(GEN.glob("vm_n*.bin.z")):
-        old.unlink()
-    if orders:
-        subset = PKG / "five_loop_subset.txt"
-        _run([_generator(), GEN] + [f"v{n}@{subset}" if n == 5 else f"v{n}" for n in orders])
+    todo = []
     for n in orders:
-        compress_programs(GEN / f"vm_n{n}.bin")
-    stamp.write_text(key)
-    return outs
+        out, stamp = GEN / f"vm_n{n}.bin.z", BUILD / f"programs_n{n}.stamp"
+        if force or not (out.exists() and stamp.exists() and stamp.read_text() == _program_key(n)):
+            todo.append(n)
+    if todo:
+        for n in todo:
+            for old in (GEN / f"vm_n{n}.bin", GEN / f"vm_n{n}.bin.z", BUILD / f"programs_n{n}.stamp"):
+                if old.exists():
+                    old.unlink()
+        subset = PKG / "five_loop_subset.txt"
+        _run([_generator(), GEN] + [f"v{n}@{subset}" if n == 5 else f"v{n}" for n in todo])
+        for n in todo:
+            compress_programs(GEN / f"vm_n{n}.bin")
+            (BUILD / f"programs_n{n}.stamp").write_text(_program_key(n))
+    return [GEN / f"vm_n{n}.bin.z" for n in orders]
 
 
 def compress_programs(raw):
