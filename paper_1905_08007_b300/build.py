@@ -39,8 +39,8 @@ INCLUDE = ROOT / "include"
 BUILD = ROOT / "_build"
 LIB = PKG / "libqedmc.so"
 DEFAULT_ORDERS = (1, 2, 3)
-# five loops (the 64-graph workload of five_loop_subset.txt, more than an
-# hour of generation on 8 cores) only on request: --programs 2 3 4 5
+# five loops (the 64-graph workload of five_loop_subset.txt, hours and close
+# to 60 GB of host memory to generate) only on request: --programs 2 3 4 5
 DEFAULT_PROGRAM_ORDERS = (2, 3, 4)
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

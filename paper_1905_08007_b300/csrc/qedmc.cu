@@ -490,10 +490,24 @@ static int vm_launch(const qed_ctx *c, const qed_ctx::VmProg &pr, const void *fn
   int T = threads;
   while (T > 32 && bytes(T) > cap) T /= 2;
   if (bytes(T) > cap) return set_err(QED_EINVAL, "program " + pr.name + " needs more shared memory than a block has");
+  int occ = 0;
+  if (dd_frame) {
+    // the double-double frame (24 bytes per register and thread) limits an
+    // SM to a few warps: take the block size, 32 to 256 threads, that keeps
+    // the most threads resident (the smaller one on a tie), e.g. one block
+    // of 128 rather than one of 64 for the largest four-loop programs
+    int best = 0;
+    for (int t = 32; t <= 256; t *= 2) {
+      if (bytes(t) > cap) break;
+      CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes(t))));
+      int o = 0;
+      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, t, bytes(t)));
+      if (o * t > best) { best = o * t; T = t; }
+    }
+  }
   L.threads = T;
   L.smem = bytes(T);
   CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L.smem)));
-  int occ = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, T, L.smem));
   L.blocks = std::max(1, occ) * c->sms;
   return QED_OK;
