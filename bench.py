@@ -251,13 +251,15 @@ def run_native(args):
     # set-up (not timed): Deg calibrated on the integrand, densities tuned
     t0 = time.perf_counter()
     diags = [ctx.load(g) for g in graphs]
-    # up to three loops: Deg calibrated on the integrand, then tuned; at four
-    # loops the calibration (too few base points for 12 lines) sends samples
-    # into corners where even double-double fails, so only the gradient
-    # tuning runs; at five loops the Deg rule is used as it is
+    # one and two loops: Deg calibrated on the integrand, then tuned; from
+    # three loops on the calibration (too few base points for 9 or 12 lines)
+    # sends samples into corners where even double-double fails (three
+    # loops, calibrated + tuned: 51 % of the samples flagged, 15 % unstable),
+    # so only the gradient tuning runs; at five loops the Deg rule is used as
+    # it is
     ts, tn = {1: (10, 1 << 21), 2: (10, 1 << 21), 3: (10, 1 << 21), 4: (4, 1 << 15), 5: (0, 0)}[args.order]
     for d in diags:
-        if args.order <= 3:
+        if args.order <= 2:
             d.calibrate_deg(n_base=8, seed=args.seed + 5)
         if ts:
             tune(d, steps=ts, n=tn, lr=0.08, seed=args.seed + 7)
@@ -335,7 +337,8 @@ def run_native(args):
                                + {4: " (one per mirror pair, bytecode integrands)",
                                   5: " (the 64-graph workload, bytecode integrands)"}.get(args.order, "") + ", "
                                f"{total:.0e} Philox samples per step shared by running variance, "
-                               + {4: "gradient-tuned Deg-rule densities", 5: "Deg-rule densities"}.get(
+                               + {3: "gradient-tuned Deg-rule densities", 4: "gradient-tuned Deg-rule densities",
+                                  5: "Deg-rule densities"}.get(
                                    args.order, "Deg-calibrated + gradient-tuned densities")
                                + ", forest-subtracted FP64 integrand, double-double re-evaluation, "
                                "persistent batched kernel (4 CUDA-graph rounds per step)",
