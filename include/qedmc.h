@@ -209,7 +209,10 @@ typedef struct {
  * else QED_EINVAL) with
  * total_samples samples in all, in one persistent launch per round: blocks
  * take (graph, counter-block) work items from a device queue, so graphs of
- * different cost share the GPU.  After round r the samples of round r+1 are
+ * different cost share the GPU; the queue holds the items of the costliest
+ * graphs first, so the blocks finish a round close together (the order
+ * changes neither a graph's samples nor the order its items are folded
+ * in).  After round r the samples of round r+1 are
  * split by the running per-sample variance and the cost model (FP64 ops per
  * sample, qed_diagram_flops, weighted by the flagged fraction).  Every graph's
  * samples are consecutive counters from 0, so a result depends only on
