@@ -1,8 +1,10 @@
 """Per-diagram subtracted AMM integrand -- oracle side (test infrastructure).
 
-What is computed (Sec. 2 items 1-4; the operator definitions are not printed
-in the paper, which defers them to its references -- the reading below is
-this project's and is listed as such in the design notes):
+What is computed (Sec. 2 items 1-4).  The paper does not print the operator
+definitions (it defers them to its references); the reading below is this
+project's own: Feynman gauge and m = 1, the F2(0) projection of item 1, the
+four operators U, L, A of item 2 with their kinematics, and the combination
+rule of item 3.
 
 1. Unsubtracted integrand M_G(z).  Feynman gauge, m = 1, alpha/pi units.  For
    an n-loop vertex graph with 3n lines, after Feynman parametrisation and the
@@ -33,8 +35,13 @@ this project's and is listed as such in the design notes):
 
 3. Combination (forest-like formula):
      A~_G = sum_F (-1)^|F| [ T(F; G) + sum_{G' in F, X in G'} T(F; G') ],
-   T(F; G'): G' gets A, every element of F u {G} strictly containing G' gets
-   (L - U), every other element of F gets U.
+   T(F; G'): G' gets A, the root G gets (L - U) when G' != G, every element
+   of F strictly containing G' gets L, every other element of F gets U.
+   (An element S with G' < S < G is both a link of the infrared chain,
+   (L - U), and the ultraviolet counterterm, U, of the block that encloses
+   it; the two add to L.  With (L - U) alone the block G/G' keeps the
+   logarithmic divergence of its subgraph S/G' -- the shell limit of the
+   three-loop rainbow graph, pinned by a test.)
 
 Parity unpinned as to the operator reading itself except through the tests
 that tie it to A_1^(2) = 1/2, the two-loop closed form, the UV/IR finiteness
@@ -434,7 +441,10 @@ def _operator_choices(g, F, gprime):
         if gprime is not None and s == gprime:
             opts_per.append([(+1, (s, "q", "F2"))])
         elif gprime is not None and s.lines(g) > gprime.lines(g):
-            opts_per.append([(+1, (s, "p", "L")), (-1, (s, "0", "UV"))])
+            # an element between G' and the root: (L - U) as a link of the
+            # infrared chain plus U as the ultraviolet counterterm of the
+            # block enclosing it -- together L
+            opts_per.append([(+1, (s, "p", "L"))])
         elif s.kind == "SE":
             opts_per.append([(+1, (s, "p", "SEmass")), (+1, (s, "k", "SEwf"))])
         else:

@@ -14,8 +14,10 @@
 //   L on a vertex-like S: on-shell forward vertex constant;
 //   A on a vertex-like S containing X: F2(0) of S;
 //   A~_G = sum_F (-1)^|F| [ T(F;G) + sum_{G' in F, X in G'} T(F;G') ],
-//   T(F;G'): G' gets A, every element of F u {G} strictly containing G' gets
-//   (L - U), every other element gets U.
+//   T(F;G'): G' gets A, the root G gets (L - U) when G' != G, every element
+//   of F strictly containing G' gets L (it is both a link of the infrared
+//   chain, L - U, and the ultraviolet counterterm U of the block around it),
+//   every other element gets U.
 // Every operator value is a block of the same Feynman parameters whose loop
 // momenta decouple from the enclosing loops (block-diagonal Lambda).
 //
@@ -189,7 +191,7 @@ static std::vector<Term> build_terms(const Graph &g) {
         const Sub &s = F[i];
         if (gp >= 0 && int(i) == gp) opts.push_back({{1, KIN_Q, PR_F2}});
         else if (gp >= 0 && (s.lines & F[gp].lines) == F[gp].lines && s.lines != F[gp].lines)
-          opts.push_back({{1, KIN_P, PR_L}, {-1, KIN_0, PR_UV}});
+          opts.push_back({{1, KIN_P, PR_L}});
         else if (s.se) opts.push_back({{1, KIN_P, PR_SEMASS}, {1, KIN_K, PR_SEWF}});
         else opts.push_back({{1, KIN_0, PR_UV}});
       }

@@ -1,7 +1,9 @@
 """Oracle pins for the subtracted integrand: the one-loop closed form and
 A_1^(2) = 1/2 (Sec. 1, Schwinger), homogeneity, mirror symmetry (Sec. 3
-footnote), pointwise UV finiteness of the forest formula (Sec. 2 item 1), and
-the Monte Carlo estimator on the one-loop graph."""
+footnote), pointwise UV finiteness of the forest formula (Sec. 2 item 1),
+integrability of every single-set limit at two loops and of the nested
+shell limits of the three-loop rainbow graph, and the Monte Carlo estimator
+on the one-loop graph."""
 import math
 
 import numpy as np
@@ -73,6 +75,53 @@ def test_uv_limits_are_integrable(gi):
             raw.append(np.abs(fu(z)) * eps ** len(L))
         assert np.all(vals[2] < 2e-2 * vals[0] + 1e-12)     # falls like eps
         assert np.all(raw[2] > 0.5 * raw[0])                  # log divergence left alone
+
+
+def _exponent(f, z0, S, e1, e2, dtype):
+    """Local exponent delta of |f| eps^|S| under z_S -> eps z_S between e1 and
+    e2, per base point: the limit is integrable where delta > 0 (a finite
+    integral needs |f| eps^|S| -> 0; a logarithmic divergence has delta 0)."""
+    out = []
+    for e in (e1, e2):
+        z = np.array(z0, dtype=dtype)
+        z[:, S] *= e
+        out.append(np.abs(np.asarray(f(z, dtype=dtype), dtype=np.float64)) * e ** len(S))
+    return np.log(out[1] / out[0]) / math.log(e2 / e1)
+
+
+@pytest.mark.parametrize("gi", range(6))
+def test_two_loop_every_single_set_limit_is_integrable(gi):
+    """Sec. 2: each graph's subtracted integrand has a finite integral.  Every
+    proper subset S of the lines, scaled to zero at two base points (all UV
+    limits, all IR limits -- a photon's parameter growing is its complement
+    shrinking -- and every mixed one), keeps |f| eps^|S| falling."""
+    g = enumerate_graphs(2)[gi]
+    f = Integrand(g)
+    z0 = np.random.default_rng(40 + gi).dirichlet([1] * 6, size=2)
+    worst = 9.0
+    for m in range(1, 63):
+        S = [l for l in range(6) if m >> l & 1]
+        d = _exponent(f, z0, S, 1e-4, 1e-6, np.longdouble)
+        worst = min(worst, float(d.min()))
+        assert np.all(d > 0.5), (S, d)
+    assert worst < 1.2
+
+
+def test_three_loop_rainbow_shell_limits_are_integrable():
+    """The three-loop rainbow graph (photons nested around X) has the two
+    nested X-subgraphs G' (lines 2, 3, photon 8) and G'' (lines 1-4, photons
+    7, 8).  The shell G''\\G' (lines 1, 4, photon 7) is a UV-divergent
+    subgraph of the block G/G' in the forest terms where G' gets A: with the
+    operator reading of item 3 (L on G'', L - U on the root) |f| eps^3 falls
+    like eps; giving G'' the operator L - U instead leaves it constant (a
+    logarithmically divergent integral)."""
+    g = enumerate_graphs(3)[47]
+    assert g.pairs == ((0, 5), (1, 4), (2, 3)) and g.e == 3
+    f = Integrand(g)
+    z0 = np.random.default_rng(5).dirichlet([1] * 9, size=2)
+    for S in ([1, 4, 7], [0, 5, 6], [0, 1, 4, 5, 6, 7], [1, 2, 3, 4, 7, 8]):
+        d = _exponent(f, z0, S, 1e-3, 1e-5, np.float64)
+        assert np.all(d > 0.8), (S, d)
 
 
 def test_mc_one_loop_within_three_sigma():
