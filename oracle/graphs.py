@@ -192,12 +192,16 @@ def i_closure(g: Graph, s) -> frozenset:
 
 
 def deg_default(g: Graph, s, c_div: float = 0.5, d_min: float = 0.05) -> float:
-    """Deg(s) reading: -omega of the I-closure when that is positive, else the
-    constant c_div for sets whose closure is UV divergent (the paper allows
-    fractional Deg below 1), floored at d_min.  Parity unpinned as to the
-    value: any positive Deg gives an unbiased estimator."""
+    """Deg(s) reading: half of -omega of the I-closure when that is positive,
+    else the constant c_div for sets whose closure is UV divergent, floored
+    at d_min.  omega counts powers of momentum; in the Feynman parameters of
+    s the integrand scales with half that power (a parameter goes like the
+    inverse square of its line's momentum), which is the exponent the bound
+    of Eq. (1) needs, and it makes Deg fractional (1/2 for one electron
+    line), as the text after Eq. (1) says Deg can be.  Parity unpinned as to
+    the value: any positive Deg gives an unbiased estimator."""
     w = -omega(g, i_closure(g, s))
-    d = float(w) if w > 0 else c_div
+    d = 0.5 * float(w) if w > 0 else c_div
     return max(d, d_min)
 
 

@@ -152,14 +152,19 @@ inline uint32_t i_closure(const Graph &g, uint32_t s) {
   return out;
 }
 
-// Deg(s) = -omega(I-closure(s)) when positive, else c_div; floored at d_min.
+// Deg(s) = -omega(I-closure(s)) / 2 when positive, else c_div; floored at
+// d_min.  omega counts momentum powers; the integrand's exponent in the
+// Feynman parameters of s is half of it (a parameter scales like the inverse
+// square of the momentum through its line), which is the exponent Eq. (1)
+// has to match to bound |f|, and what makes Deg fractional (1/2 for a
+// single electron line).
 inline std::vector<double> deg_table(const Graph &g, double c_div = 0.5, double d_min = 0.05) {
   int N = g.n_lines();
   uint32_t full = (1u << N) - 1;
   std::vector<double> d(size_t(1) << N, 0.0);
   for (uint32_t m = 1; m < full; ++m) {
     int w = -omega(g, i_closure(g, m));
-    double v = w > 0 ? double(w) : c_div;
+    double v = w > 0 ? 0.5 * double(w) : c_div;
     d[m] = std::max(v, d_min);
   }
   return d;
