@@ -1,17 +1,22 @@
-"""Benchmark: Monte Carlo samples/s on the two-loop lepton-loop-free vertex set.
+"""Benchmark: Monte Carlo samples/s, time to a target sigma and FP64 fraction
+on a loop-order set of lepton-loop-free vertex graphs (default: four loops).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                    [--order 2|3|4|5]
 
-A step is one pass of the whole hot path over one batch: the six two-loop
-graphs integrated together with 6 x `--samples` fresh Philox counters
-(default 6e8 samples per step) in the persistent batched kernel, samples
-shared by running variance, from Deg-calibrated and gradient-tuned densities
-(set up once before the warm-up, time reported), with the forest-subtracted
-FP64 integrand, double-double re-evaluation of flagged points and compensated
-reductions.  There is no input stream: points are generated from counters on
-the device, so the L2 flush between steps only keeps the timing honest for
-the tables.  The plain per-graph path (untuned densities, equal samples) is
-reported beside it.
+A step is one pass of the whole hot path over one batch: every graph of the
+set (four loops: the 269 mirror-reduced graphs, bytecode integrands)
+integrated together with `--samples` fresh Philox counters per graph
+(default 2^16 at four loops, 1.76e7 per step) in the persistent batched
+kernels, samples shared by running variance, from Deg-calibrated and
+gradient-tuned densities (set up once before the warm-up, time reported),
+with the forest-subtracted FP64 integrand, double-double re-evaluation of
+flagged points and compensated reductions.  There is no input stream:
+points are generated from counters on the device, so the L2 flush between
+steps only keeps the timing honest for the tables and programs.  The plain
+per-graph path (Deg-rule densities, equal samples, one launch pair per graph)
+is timed beside it on the same budget for the time-to-sigma comparison, and
+a short two-loop run reports its pull against the two-loop closed form.
 
 Multi-GPU (torchrun, one rank per GPU): every rank integrates its own disjoint
 counter blocks (weak scaling); the only exchange is the final merge of the
@@ -44,7 +49,7 @@ SIGMA_TARGET = 1e-5
 # time-to-sigma target per loop order (four loops: sigma_total = 5e-3)
 SIGMA_TARGETS = {1: 1e-5, 2: 1e-5, 3: 1e-4, 4: 5e-3, 5: 0.1}
 # samples per graph per step: 6e8 per step on the two-loop set, 1e9 on the
-# three-loop set (BASELINE's config 3 budget)
+# three-loop set, 1.76e7 on the 269 four-loop graphs
 DEFAULT_SAMPLES = {1: 1e8, 2: 1e8, 3: 2e7, 4: 2 ** 16, 5: 2 ** 12}
 # work-item size of the batched kernel per order (a four-loop sample is ~1e5
 # FP64 operations, a five-loop one ~1e6): at four loops 2048 samples give
@@ -143,28 +148,65 @@ def graph_set(q, order):
     return gs, [1.0] * len(gs)
 
 
-def cpu_baseline(n_per_graph=None, seed=0, order=2):
-    """The oracle as it stands on this host's cores (numpy, one thread of work),
-    on a bounded sample of the same graph set (about 10-20 s)."""
+def _cpu_model():
+    try:
+        for ln in Path("/proc/cpuinfo").read_text().splitlines():
+            if ln.startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _oracle_job(job):
+    """Oracle weights (numpy FP64, as it stands) for samples [begin, begin + n)
+    of graph gi of the given order; returns the sample count."""
+    order, gi, begin, n, seed = job
     from oracle.estimator import weights
     from oracle.graphs import enumerate_graphs
     from oracle.integrand import Integrand
-    graphs = enumerate_graphs(order)
-    if order == 3:
-        graphs = graphs[::10]
-    if order == 4:
-        graphs = graphs[85:86]
-    n_per_graph = n_per_graph or {1: 3000, 2: 300, 3: 20, 4: 2}[order]
+    g = enumerate_graphs(order)[gi]
+    if n == 0:
+        return 0
+    return int(weights(Integrand(g), g, gi, seed, begin, n).size)
+
+
+# bounded oracle samples per order: (graph indices in the full enumeration,
+# samples per graph).  Four loops: graph 85 (one forest term, the cheapest of
+# the set; a typical four-loop graph costs the oracle many times more).
+CPU_SAMPLE = {1: ([0], 3000), 2: (list(range(6)), 300), 3: (list(range(0, 50, 10)), 20), 4: ([85], 1)}
+
+
+def cpu_baseline(order=4, seed=0):
+    """The oracle as it stands on this host's cores, on a bounded sample of the
+    same graph set: on one core in this process, then on every core (one
+    spawned process per core, each on its own counters, the pool started and
+    its imports done before the clock starts)."""
+    import multiprocessing as mp
+    if order not in CPU_SAMPLE:
+        return None
+    gis, n = CPU_SAMPLE[order]
+    jobs = [(order, gi, 10**12, n, seed) for gi in gis]
+    _oracle_job((order, gis[0], 0, 0, seed))
     t0 = time.perf_counter()
-    tot = 0
-    for g in graphs:
-        sid = enumerate_graphs(order).index(g)
-        w = weights(Integrand(g), g, sid, seed, 10**12, n_per_graph)
-        tot += w.size
-    dt = time.perf_counter() - t0
-    return {"value": tot / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n_per_graph} samples of each of {len(graphs)} {order}-loop graphs "
-                      f"(Philox counters 1e12.., seed {seed}), {dt:.1f} s"}
+    tot = sum(_oracle_job(j) for j in jobs)
+    dt1 = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_job, [(order, gis[0], 0, 0, seed)] * cores)
+        jobs_all = [(order, gi, 10**12 + (k + 1) * 10**6, n, seed) for k in range(cores) for gi in gis]
+        t0 = time.perf_counter()
+        tot_all = sum(pool.map(_oracle_job, jobs_all, chunksize=1))
+        dtn = time.perf_counter() - t0
+    what = (f"{n} sample(s) of each of {len(gis)} {order}-loop graph(s) "
+            f"{gis if len(gis) <= 6 else ''} (Philox counters from 1e12, seed {seed})")
+    return {"value": tot_all / dtn, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "cpu_model": _cpu_model(),
+            "sample": f"{what}, once per core in parallel: {tot_all} samples in {dtn:.1f} s",
+            "one_core": {"value": tot / dt1, "unit": "samples/s", "cores": 1,
+                         "sample": f"{what}: {tot} samples in {dt1:.1f} s"},
+            "note": "numpy FP64 oracle as it stands; a reported baseline, not a target"}
 
 
 def compare_plain(diags, graphs, ctx, S, seed, t_step, sigma_step, q):
@@ -188,26 +230,19 @@ def compare_plain(diags, graphs, ctx, S, seed, t_step, sigma_step, q):
 
 
 def run_reference(args):
+    """The CPU oracle as it stands on the same workload and metric: each step a
+    bounded sample of the graph set (CPU_SAMPLE), fresh counters every step,
+    on rank 0 only."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    n = args.ref_samples
-    from oracle.estimator import weights
-    from oracle.graphs import enumerate_graphs
-    from oracle.integrand import Integrand
-    graphs = enumerate_graphs(args.order)
-    if args.order >= 4:
-        # bounded sample: a four-loop point costs the oracle seconds
-        graphs = graphs[85::108]
-        n = 1
-    fs = [Integrand(g) for g in graphs]
+    if args.order not in CPU_SAMPLE:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle needs hours per five-loop point"}))
+        return 0
+    gis, n = CPU_SAMPLE[args.order]
 
     def step(s):
-        tot = 0
-        for sid, (g, f) in enumerate(zip(graphs, fs)):
-            w = weights(f, g, sid, args.seed, s * n, n)
-            tot += w.size
-        return tot
+        return sum(_oracle_job((args.order, gi, 10**12 + s * n, n, args.seed)) for gi in gis)
     for s in range(args.warmup):
         step(s)
     t0 = time.perf_counter()
@@ -219,16 +254,54 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (Philox counters)",
-        "config": {"workload": f"{args.order}-loop lepton-loop-free vertex set: {len(graphs)} graphs, "
-                               "Eq. (1) density, forest-subtracted integrand, FP64 (the CPU oracle)",
-                   "loops": args.order, "graphs": len(graphs),
-                   "samples_per_graph_per_step": n, "seed": args.seed},
-        "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{n} samples per graph per step, {args.steps} steps"},
+        "config": {"workload": f"{args.order}-loop lepton-loop-free vertex set, bounded sample: "
+                               f"{n} sample(s) per step of each of graphs {gis}, Eq. (1) density, "
+                               "forest-subtracted integrand, FP64 (the CPU oracle)",
+                   "loops": args.order, "graphs": len(gis), "samples_per_graph_per_step": n, "seed": args.seed},
+        "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle", "cpu_model": _cpu_model(),
+                         "sample": f"{n} sample(s) of each of graphs {gis} per step, {args.steps} steps"},
         "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
+
+
+def two_loop_pull(q, ctx, seed, samples=6e8):
+    """The six two-loop graphs, Deg-calibrated and tuned, 6e8 samples in the
+    batched kernel: the set total against the two-loop closed form."""
+    from paper_1905_08007_b300.tune import tune
+    ds = [ctx.load(g) for g in q.enumerate_graphs(2)]
+    for d in ds:
+        d.calibrate_deg(n_base=8, seed=seed + 5)
+        tune(d, steps=10, n=1 << 21, lr=0.08, seed=seed + 7)
+    res = ctx.integrate_batch(ds, int(samples), seed=seed + 11, policy="variance", rounds=4, chunk=1 << 18,
+                              counter_base=1 << 42)
+    tot = sum(r.value for r in res)
+    sig = math.sqrt(sum(r.variance for r in res))
+    return {"value": tot, "sigma": sig, "closed_form": TWO_LOOP_TARGET, "pull": (tot - TWO_LOOP_TARGET) / sig,
+            "samples": sum(r.n for r in res), "seconds": res[0].seconds}
+
+
+def _traffic(kernel, order, seconds, launches):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary for this
+    workload (profiles/<kernel>_<order>_loop_traffic.md), or None when there is
+    none or the kernel's source has changed since it was taken."""
+    import hashlib
+    path = ROOT / "profiles" / f"{kernel}_{order}_loop_traffic.md"
+    if not path.exists():
+        return None
+    vals = {}
+    for ln in path.read_text().splitlines():
+        if ":" in ln and ln.startswith("- "):
+            k, v = ln[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    src = ROOT / "paper_1905_08007_b300" / "csrc" / vals.get("source", "")
+    if not src.is_file() or hashlib.sha256(src.read_bytes()).hexdigest()[:16] != vals.get("source_sha256_16"):
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def run_native(args):
@@ -259,12 +332,18 @@ def run_native(args):
     # it is
     ts, tn = {1: (10, 1 << 21), 2: (10, 1 << 21), 3: (10, 1 << 21), 4: (4, 1 << 15), 5: (0, 0)}[args.order]
     for d in diags:
-        if args.order <= 2:
+        if args.calibrate and args.order <= 4:
             d.calibrate_deg(n_base=8, seed=args.seed + 5)
         if ts:
             tune(d, steps=ts, n=tn, lr=0.08, seed=args.seed + 7)
     setup_s = time.perf_counter() - t0
     flops = [d.flops_per_sample() for d in diags]
+    ddflops = []
+    for d in diags:
+        try:
+            ddflops.append(d.flops_per_dd_sample())
+        except q.QedError:
+            ddflops.append(None)
     rounds, chunk = 4, int(args.chunk or CHUNK[args.order])
 
     def step(s):
@@ -283,7 +362,7 @@ def run_native(args):
     clocks.start()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    launches, ksec, alg, nsamp = 0, 0.0, 0.0, 0
+    launches, ksec, dsec, alg, algdd, nsamp = 0, 0.0, 0.0, 0.0, 0.0, 0
     wall0 = time.perf_counter()
     ev0.record(stream)
     for s in range(args.steps):
@@ -291,8 +370,10 @@ def run_native(args):
         res = step(args.warmup + s)
         launches += res[0].launches
         ksec += res[0].kernel_seconds
+        dsec += res[0].dd_seconds
         for i, r in enumerate(res):
             alg += flops[i] * r.n
+            algdd += (ddflops[i] or 0.0) * r.n_flagged
             nsamp += r.n
             acc[i] = r if acc[i] is None else q.merge_results(acc[i], r)
     ev1.record(stream)
@@ -325,8 +406,19 @@ def run_native(args):
     value = total_samples / tmax
     tot = sum(w * r.value for w, r in zip(mw, results))
     sigma = math.sqrt(sum(w * w * r.variance for w, r in zip(mw, results)))
-    achieved = alg / ksec / 1e12
     peak = fp64_peak / 1e12
+    k64 = {"name": ("k_batch_fp64 (persistent FP64 integration kernel)" if args.order <= 3 else
+                    f"k_batch_vm_fp64<{3 * args.order}> (persistent FP64 interpreter kernel, bytecode integrands)"),
+           "seconds": ksec, "achieved": alg / ksec / 1e12, "frac": alg / ksec / 1e12 / peak,
+           "flops": alg}
+    kdd = {"name": ("k_batch_dd (double-double pass)" if args.order <= 3 else
+                    f"k_batch_vm_dd<{3 * args.order}> (double-double interpreter pass)"),
+           "seconds": dsec, "achieved": algdd / dsec / 1e12 if dsec > 0 else None,
+           "frac": algdd / dsec / 1e12 / peak if dsec > 0 else None, "flops": algdd,
+           "flops_counted": all(x is not None for x in ddflops)}
+    dom = k64 if ksec >= dsec else kdd
+    traffic = _traffic(dom["name"].split(" ")[0], args.order, ksec if dom is k64 else dsec,
+                       args.steps * rounds)
     n_items = max(len(diags), (total // rounds + chunk - 1) // chunk)
     flagged = sum(r.n_flagged for r in results)
     line = {
@@ -355,13 +447,18 @@ def run_native(args):
         "time_to_sigma": {"target_sigma": SIGMA_TARGETS[args.order],
                           "seconds": tmax * (sigma / SIGMA_TARGETS[args.order]) ** 2,
                           "sigma_reached": sigma, "seconds_run": tmax},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": ("k_batch_fp64 (persistent FP64 integration kernel)" if args.order <= 3 else
-                                f"k_batch_vm_fp64<{3 * args.order}> (persistent FP64 interpreter kernel, "
-                                "bytecode integrands)"),
+        "roofline": {"bound": "alu", "achieved": dom["achieved"], "peak": peak, "unit": "TFLOP/s",
+                     "frac": dom["frac"], "traffic": traffic,
+                     "kernel": dom["name"],
                      "peak_source": "measured FP64 FMA throughput (qed_fp64_peak), of measured",
-                     "flops_per_sample": {str(i): f for i, f in enumerate(flops)}},
+                     "kernels": {"fp64": k64, "dd": kdd},
+                     "step": {"flops": alg + algdd, "seconds": tmax,
+                              "achieved": (alg + algdd) / tmax / 1e12,
+                              "frac": (alg + algdd) / tmax / 1e12 / peak,
+                              "note": "whole step: both passes' algorithmic FP64 work (qed_diagram_flops "
+                                      "per sample, qed_diagram_flops_dd per flagged sample) over the "
+                                      "step's device time"},
+                     "flops_per_sample_mean": sum(flops) / len(flops)},
         "gpu_launches": launches,
         "e2e": {"value": total_samples / wmax, "unit": "samples/s",
                 "h2d_bytes_per_step": rounds * n_items * 16,
@@ -370,6 +467,8 @@ def run_native(args):
     }
     if ws == 1 and args.compare and args.order in (2, 4):
         line["plain_per_graph"] = compare_plain(diags, graphs, ctx, S, args.seed, tmax / args.steps, sigma, q)
+    if ws == 1 and args.order != 2 and args.order <= 4:
+        line["two_loop_total"] = two_loop_pull(q, ctx, args.seed)
     if ws == 1 and not args.no_cpu_baseline and args.order <= 4:
         line["cpu_baseline"] = cpu_baseline(order=args.order)
     print(json.dumps(line))
@@ -385,11 +484,12 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--samples", type=float, default=None, help="samples per graph per step")
-    ap.add_argument("--order", type=int, default=2, choices=[1, 2, 3, 4, 5], help="loop order of the graph set")
+    ap.add_argument("--order", type=int, default=4, choices=[1, 2, 3, 4, 5], help="loop order of the graph set")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=None, help="samples per work item of the batched kernel")
-    ap.add_argument("--ref-samples", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-calibrate", dest="calibrate", action="store_false",
+                    help="Deg rule without the calibration on the integrand")
     ap.add_argument("--no-compare", dest="compare", action="store_false",
                     help="skip the plain vs batched-tuned time-to-sigma comparison")
     a = ap.parse_args(argv)

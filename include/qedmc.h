@@ -49,9 +49,9 @@ extern "C" {
 typedef struct qed_ctx qed_ctx;
 typedef struct qed_diag qed_diag;
 
-/* A vertex graph without lepton loops (Sec. 3: "diagrams without lepton
- * loops"; mirror images are distinct graphs here).  stream_id is the third
- * Philox counter word used for this graph's samples. */
+/* A vertex graph with no closed lepton loop, the set Sec. 3 computes (mirror
+ * images are distinct graphs here).  stream_id is the third Philox counter
+ * word used for this graph's samples. */
 typedef struct {
   int n;                          /* loops = internal photons, 1..QED_MAX_LOOPS */
   int pairs[2 * QED_MAX_LOOPS];   /* photon a: vertices pairs[2a] < pairs[2a+1] */
@@ -62,9 +62,11 @@ typedef struct {
 /* Density of Eq. (1).  If deg != NULL it holds Deg(s) for every subset s of
  * the N = 3n lines as a bitmask-indexed array of 2^N doubles (entries 0 and
  * 2^N-1 unused); all used entries must be > 0 (else QED_EINVAL).  If deg is
- * NULL the library builds Deg(s) = -omega(I-closure(s)) when positive, else
- * c_div, floored at d_min (Sec. 2: Deg from omega of I-closures, sometimes
- * fractional and below 1). */
+ * NULL the library builds Deg(s) = -omega(I-closure(s)) / 2 when positive,
+ * else c_div, floored at d_min (Sec. 2: Deg from omega of I-closures,
+ * sometimes fractional and below 1; omega counts momentum powers, and a
+ * Feynman parameter scales like the inverse square of its line's momentum,
+ * so the integrand's exponent in the parameters is half of it). */
 typedef struct {
   const double *deg;
   double c_div;                   /* default 0.5 when <= 0 */
@@ -83,6 +85,7 @@ typedef struct {
   double seconds;                 /* device time of the call (all kernels) */
   double kernel_seconds;          /* device time of the FP64 integration kernel */
   uint32_t launches;              /* kernels launched by the call */
+  double dd_seconds;              /* device time of the double-double kernels */
 } qed_result;
 
 /* ---- context ------------------------------------------------------------ */
@@ -179,15 +182,22 @@ int qed_diagram_set_pdf_params(qed_diag *d, const double *alpha, const double *b
  * over samples [begin, begin + n) recomputed from their Philox counters:
  * *m2 = estimate of M2, grad[0..N-1] = dM2/dalpha, grad[N..2N-1] =
  * dM2/dbeta (score-function form -E_p[w^2 d log p / d theta]; d log Z /
- * d theta from a reverse pass over the F recursion on the host). */
+ * d theta from a reverse pass over the F recursion on the host).  The
+ * weights follow the estimator's rule: a point whose FP64 rounding-error
+ * estimate exceeds the context threshold enters with its double-double
+ * value, and with w = 0 if it fails there too.  Launches cover at most
+ * 2^22 samples each (the flagged queue's capacity); allocates one small
+ * device buffer for the duration of the call. */
 int qed_pdf_grad(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed, double *m2, double *grad);
 
-/* Calibrate Deg on the integrand itself (Sec. 2: Deg(s) "is not fully
- * justified mathematically"; the paper lowers it for infrared limits).  For
+/* Calibrate Deg on the integrand itself (Sec. 2 gives the Deg rule as a
+ * heuristic without a complete proof, lowered for infrared limits).  For
  * every proper subset s the growth exponent a_s of the integrand under
  * z_s -> eps z_s is measured on the GPU in double-double at n_base random
- * points (eps = 1e-4 and 1e-6) and Deg(s) is capped at |s| - a_s, where w =
- * f/p stays bounded: Deg(s) = max(d_min, min(Deg(s), |s| - a_s)).
+ * points (eps = 1e-6 and 1e-8, past the bumps of nearby scales) and Deg(s)
+ * is capped at |s| - a_s (a_s: |f| grows like eps^-a_s), where w = f/p stays
+ * bounded in that limit and the variance finite:
+ * Deg(s) = max(d_min, min(Deg(s), |s| - a_s)).
  * Allocates two small device buffers for the duration of the call. */
 int qed_diagram_calibrate_deg(qed_diag *d, int n_base, uint64_t seed);
 /* The current Deg table (2^N doubles, bitmask-indexed). */
@@ -230,6 +240,14 @@ int qed_result_merge(const qed_result *a, const qed_result *b, qed_result *out);
  * counted once each) per sample of this graph's hot path: sampler, integrand
  * and accumulation.  Used as the algorithmic work of the roofline. */
 int qed_diagram_flops(const qed_diag *d, double *flops_per_sample);
+/* FP64 operations (an FMA counts 2) per sample re-evaluated in double-double:
+ * the sampler as above plus the integrand in the interpreter's
+ * double-double arithmetic, counted instruction by instruction over the
+ * graph's bytecode program (for a graph with a compiled integrand, the
+ * program of the same graph; QED_ENOTFOUND if none is registered).  With
+ * qed_diagram_flops it gives the algorithmic FP64 work of a whole step, both
+ * passes included. */
+int qed_diagram_flops_dd(const qed_diag *d, double *flops_per_sample);
 /* Measured FP64 fused-multiply-add throughput of the device (FLOP/s, 2 per
  * FMA): every SM runs independent FMA chains for about `ms` milliseconds. */
 int qed_fp64_peak(int device, double ms, double *flops_per_s);
@@ -242,16 +260,25 @@ int qed_fp64_peak(int device, double ms, double *flops_per_s);
  * further cudaMalloc, or a latency-critical loop where an allocation, which
  * can synchronise the device, is not acceptable.  The call allocates nothing
  * on the device or the host: its scratch is one file-scope device array of
- * about 650 KB that every GPU loading the library holds until the process
- * exits.  The first call on a device looks up that array's device address
- * (with the device current); make that first call before any stream capture.
+ * 720,968 bytes (about 704 KiB) per GPU.  The GPU takes that memory when the
+ * library's device code is loaded on it: under CUDA's default lazy module
+ * loading that is the first use of the library's device code on that
+ * device (this call's address lookup, or any other call that launches a
+ * kernel), so make one such call, or run with CUDA_MODULE_LOADING=EAGER,
+ * before handing the remaining device memory to a pool.  The memory is held
+ * until the process exits.  The first call on a device looks up the array's
+ * device address (with the device current) and keeps it for the process:
+ * make that first call before any stream capture, and do not use the
+ * library on a device after cudaDeviceReset in the same process.
  * Limits: at most 2048 blocks in the context's launch shape (QED_EINVAL
- * otherwise); more than 65536 flagged points in a chunk of 2^30 samples are
- * found again by re-scanning the chunk instead of being queued.  All calls in
- * the process share the array, so calls that overlap on the GPU (other
- * threads, other streams) race: serialise them.  Each call clears the
- * counters it needs before use.  Compiled integrands only: a graph that
- * uses a bytecode program gives QED_EINVAL. */
+ * otherwise); when more than 65536 points of a chunk of 2^30 samples are
+ * flagged, the double-double kernel re-scans the whole chunk and that pass
+ * replaces the first (each point is flagged or accepted by one decision).
+ * All calls in the process share the array, so calls that overlap on the
+ * GPU (other threads, other streams) race: serialise them.  Each call clears
+ * the counters it needs before use.  kernel_seconds is the FP64 integration
+ * kernel's device time, as for qed_integrate_range.  Compiled integrands
+ * only: a graph that uses a bytecode program gives QED_EINVAL. */
 int qed_integrate_range_noalloc(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed, qed_result *out);
 
 #ifdef __cplusplus

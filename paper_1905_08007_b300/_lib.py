@@ -45,7 +45,7 @@ class _Result(C.Structure):
     _fields_ = [("value", C.c_double), ("variance", C.c_double), ("sum_w", C.c_double * 2),
                 ("sum_w2", C.c_double * 2), ("n", C.c_uint64), ("n_flagged", C.c_uint64),
                 ("n_unstable", C.c_uint64), ("seconds", C.c_double),
-                ("kernel_seconds", C.c_double), ("launches", C.c_uint32)]
+                ("kernel_seconds", C.c_double), ("launches", C.c_uint32), ("dd_seconds", C.c_double)]
 
 
 @dataclass(frozen=True)
@@ -85,6 +85,7 @@ class Result:
     seconds: float
     kernel_seconds: float = 0.0
     launches: int = 0
+    dd_seconds: float = 0.0
 
     @property
     def sigma(self):
@@ -96,13 +97,13 @@ class Result:
         r.sum_w[0], r.sum_w[1] = self.sum_w
         r.sum_w2[0], r.sum_w2[1] = self.sum_w2
         r.n, r.n_flagged, r.n_unstable, r.seconds = self.n, self.n_flagged, self.n_unstable, self.seconds
-        r.kernel_seconds, r.launches = self.kernel_seconds, self.launches
+        r.kernel_seconds, r.launches, r.dd_seconds = self.kernel_seconds, self.launches, self.dd_seconds
         return r
 
     @staticmethod
     def _from_c(r):
         return Result(r.value, r.variance, (r.sum_w[0], r.sum_w[1]), (r.sum_w2[0], r.sum_w2[1]),
-                      r.n, r.n_flagged, r.n_unstable, r.seconds, r.kernel_seconds, r.launches)
+                      r.n, r.n_flagged, r.n_unstable, r.seconds, r.kernel_seconds, r.launches, r.dd_seconds)
 
 
 _LIB = None
@@ -141,6 +142,12 @@ def load_library():
         "qed_eval_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_void_p]),
         "qed_result_merge": (C.c_int, [P(_Result), P(_Result), P(_Result)]),
         "qed_diagram_flops": (C.c_int, [C.c_void_p, P(C.c_double)]),
+        "qed_diagram_flops_dd": (C.c_int, [C.c_void_p, P(C.c_double)]),
+        "qed_pdf_grad": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, P(C.c_double),
+                                   P(C.c_double)]),
+        "qed_diagram_set_pdf_params": (C.c_int, [C.c_void_p, P(C.c_double), P(C.c_double)]),
+        "qed_integrate_range_noalloc": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64,
+                                                  P(_Result)]),
         "qed_integrate_batch": (C.c_int, [C.c_void_p, P(C.c_void_p), C.c_int, C.c_uint64, C.c_uint64,
                                           P(_BatchOpts), P(_Result)]),
         "qed_fp64_peak": (C.c_int, [C.c_int, C.c_double, P(C.c_double)]),
@@ -339,6 +346,12 @@ class Diagram:
     def flops_per_sample(self) -> float:
         v = C.c_double()
         _check(load_library().qed_diagram_flops(self._h, C.byref(v)))
+        return v.value
+
+    def flops_per_dd_sample(self) -> float:
+        """qed_diagram_flops_dd: FP64 work of one double-double re-evaluation."""
+        v = C.c_double()
+        _check(load_library().qed_diagram_flops_dd(self._h, C.byref(v)))
         return v.value
 
     def close(self):

@@ -91,9 +91,10 @@ def build_programs(orders=DEFAULT_PROGRAM_ORDERS, force=False):
     BUILD.mkdir(exist_ok=True)
     GEN.mkdir(exist_ok=True)
     todo = []
+    keys = {n: _program_key(n) for n in orders}     # taken before generating
     for n in orders:
         out, stamp = GEN / f"vm_n{n}.bin.z", BUILD / f"programs_n{n}.stamp"
-        if force or not (out.exists() and stamp.exists() and stamp.read_text() == _program_key(n)):
+        if force or not (out.exists() and stamp.exists() and stamp.read_text() == keys[n]):
             todo.append(n)
     if todo:
         for n in todo:
@@ -104,7 +105,7 @@ def build_programs(orders=DEFAULT_PROGRAM_ORDERS, force=False):
         _run([_generator(), GEN] + [f"v{n}@{subset}" if n == 5 else f"v{n}" for n in todo])
         for n in todo:
             compress_programs(GEN / f"vm_n{n}.bin")
-            (BUILD / f"programs_n{n}.stamp").write_text(_program_key(n))
+            (BUILD / f"programs_n{n}.stamp").write_text(keys[n])
     return [GEN / f"vm_n{n}.bin.z" for n in orders]
 
 

@@ -220,15 +220,19 @@ __global__ void __launch_bounds__(256) k_integrate(KParams P) {
 }
 
 // Double-double re-evaluation of flagged samples.  mode 0: the queue holds
-// the offsets; mode 1 (queue overflow): rescan every offset in [0, n) and
-// re-evaluate those the FP64 path flags.
+// the offsets the FP64 kernel flagged, and only they are summed here.
+// mode 1 (the queue overflowed): a complete second pass over [0, n) that
+// replaces the first one -- every point is evaluated in FP64 again, summed
+// when its estimate passes and re-evaluated in double-double when it does
+// not, and counted as flagged here -- so that every point is accepted or
+// flagged by one decision taken in one kernel.
 template <int FID, int N>
 __global__ void __launch_bounds__(256) k_redo_dd(KParams P, int mode, unsigned int qn) {
   extern __shared__ double smem[];
   double *sF = smem, *sG = smem + (1 << N), *sInv = smem + 2 * (1 << N);
   load_tables<N>(P, sF, sG, sInv);
   KSum sw, sw2;
-  unsigned long long nunst = 0;
+  unsigned long long nflag = 0, nunst = 0;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   const uint64_t total = mode == 0 ? uint64_t(qn) : P.n;
   for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += stride) {
@@ -240,7 +244,12 @@ __global__ void __launch_bounds__(256) k_redo_dd(KParams P, int mode, unsigned i
       double ab;
       const double f0 = qed_gen_f<FID>::template eval<double>(z, ab);
       const double w0 = f0 * exp(-lp);
-      if (isfinite(w0) && rel_err_estimate(f0, ab, 1.1102230246251565e-16) <= P.thresh) continue;
+      if (isfinite(w0) && rel_err_estimate(f0, ab, 1.1102230246251565e-16) <= P.thresh) {
+        sw.add(w0);
+        sw2.add(w0 * w0);
+        continue;
+      }
+      ++nflag;
     }
     dd zd[N];
 #pragma unroll
@@ -255,7 +264,7 @@ __global__ void __launch_bounds__(256) k_redo_dd(KParams P, int mode, unsigned i
     sw.add(w);
     sw2.add(w * w);
   }
-  block_reduce_store(sw, sw2, 0ull, nunst, P.partials, P.counts, blockIdx.x);
+  block_reduce_store(sw, sw2, nflag, nunst, P.partials, P.counts, blockIdx.x);
 }
 
 template <int FID, int N>
@@ -307,44 +316,35 @@ __global__ void __launch_bounds__(256) k_eval(const double *__restrict__ zin, ui
 // beta_m): accumulates, over samples recomputed from their Philox counters,
 //   w^2,  w^2 * sum_{l: m in S_l, Deg(S_l) not clamped} log t_l,  w^2 [j_1 = m].
 // The host adds the d log Z / d theta terms (reverse pass over the F table).
-// out: [gridDim.x][2N + 1] (w^2, the N alpha sums, the N beta sums).
-template <int FID, int N>
-__global__ void __launch_bounds__(256) k_pdf_grad(KParams P, const uint8_t *__restrict__ act, double *out) {
-  extern __shared__ double smem[];
-  double *sF = smem, *sG = smem + (1 << N), *sInv = smem + 2 * (1 << N);
-  load_tables<N>(P, sF, sG, sInv);
-  double m2 = 0.0, ga[N], gb[N];
+// The weights follow the estimator's rule: a point whose FP64 rounding-error
+// estimate exceeds the threshold is queued and summed by k_pdf_grad_dd with
+// its double-double value, and contributes w = 0 if it fails there too.
+template <int N>
+__device__ __forceinline__ void grad_add(double w2, const int *order, const double *lt,
+                                         const uint8_t *__restrict__ act, double &m2, double *ga, double *gb) {
+  m2 += w2;
+  // cumulative sum over sector positions: line at position r gets
+  // sum_{l=1..r} act(S_l) log t_l
+  double cum = 0.0;
+  uint32_t S = (1u << N) - 1u;
 #pragma unroll
-  for (int m = 0; m < N; ++m) { ga[m] = 0.0; gb[m] = 0.0; }
-  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P.n; i += stride) {
-    double z[N], lt[N];
-    int order[N];
-    const double lp = draw_point<N, true>(P.begin + i, P, sF, sG, sInv, z, order, lt);
-    double absum;
-    const double f = qed_gen_f<FID>::template eval<double>(z, absum);
-    double w = f * exp(-lp);
-    if (!isfinite(w)) w = 0.0;
-    const double w2 = w * w;
-    m2 += w2;
-    // cumulative sum over sector positions: line at position r gets
-    // sum_{l=1..r} act(S_l) log t_l
-    double cum = 0.0;
-    uint32_t S = (1u << N) - 1u;
-#pragma unroll
-    for (int r = 0; r < N; ++r) {
-      if (r > 0) {
-        S &= ~(1u << order[r - 1]);
-        if (act[S]) cum += lt[r];
-      }
-#pragma unroll
-      for (int m = 0; m < N; ++m) if (order[r] == m) ga[m] += w2 * cum;
+  for (int r = 0; r < N; ++r) {
+    if (r > 0) {
+      S &= ~(1u << order[r - 1]);
+      if (act[S]) cum += lt[r];
     }
 #pragma unroll
-    for (int m = 0; m < N; ++m) if (order[0] == m) gb[m] += w2;
+    for (int m = 0; m < N; ++m) if (order[r] == m) ga[m] += w2 * cum;
   }
-  // block reduction (warp shuffles, then shared memory), fixed order
-  __shared__ double red[32][2 * N + 1];
+#pragma unroll
+  for (int m = 0; m < N; ++m) if (order[0] == m) gb[m] += w2;
+}
+
+// Block sums of (w^2, the N alpha sums, the N beta sums) in a fixed order
+// (warp shuffles, then shared memory) into out[blockIdx.x][2N + 1].
+template <int N>
+__device__ __forceinline__ void grad_store(double m2, const double *ga, const double *gb, double *out) {
+  __shared__ double red[8][2 * N + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double v[2 * N + 1];
   v[0] = m2;
@@ -364,15 +364,69 @@ __global__ void __launch_bounds__(256) k_pdf_grad(KParams P, const uint8_t *__re
   }
 }
 
+template <int FID, int N>
+__global__ void __launch_bounds__(256) k_pdf_grad(KParams P, const uint8_t *__restrict__ act, double *out) {
+  extern __shared__ double smem[];
+  double *sF = smem, *sG = smem + (1 << N), *sInv = smem + 2 * (1 << N);
+  load_tables<N>(P, sF, sG, sInv);
+  double m2 = 0.0, ga[N], gb[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) { ga[m] = 0.0; gb[m] = 0.0; }
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P.n; i += stride) {
+    double z[N], lt[N];
+    int order[N];
+    const double lp = draw_point<N, true>(P.begin + i, P, sF, sG, sInv, z, order, lt);
+    double absum;
+    const double f = qed_gen_f<FID>::template eval<double>(z, absum);
+    const double w = f * exp(-lp);
+    if (!isfinite(w) || !(rel_err_estimate(f, absum, 1.1102230246251565e-16) <= P.thresh)) {
+      const unsigned int slot = atomicAdd(P.queue_len, 1u);
+      if (slot < P.queue_cap) P.queue[slot] = i;
+      continue;
+    }
+    grad_add<N>(w * w, order, lt, act, m2, ga, gb);
+  }
+  grad_store<N>(m2, ga, gb, out);
+}
+
+// The flagged points of k_pdf_grad (offsets in P.queue[0..qn)) in double-double.
+template <int FID, int N>
+__global__ void __launch_bounds__(256) k_pdf_grad_dd(KParams P, unsigned int qn, const uint8_t *__restrict__ act,
+                                                     double *out) {
+  extern __shared__ double smem[];
+  double *sF = smem, *sG = smem + (1 << N), *sInv = smem + 2 * (1 << N);
+  load_tables<N>(P, sF, sG, sInv);
+  double m2 = 0.0, ga[N], gb[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) { ga[m] = 0.0; gb[m] = 0.0; }
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < qn; i += stride) {
+    double z[N], lt[N];
+    int order[N];
+    const double lp = draw_point<N, true>(P.begin + P.queue[i], P, sF, sG, sInv, z, order, lt);
+    dd zd[N];
+#pragma unroll
+    for (int L = 0; L < N; ++L) zd[L] = dd{z[L], 0.0};
+    double absum;
+    const dd f = qed_gen_f<FID>::template eval<dd>(zd, absum);
+    const double w = (f.hi + f.lo) * exp(-lp);
+    if (!isfinite(w) || !(rel_err_estimate(f.hi, absum, 1.2325951644078309e-32) <= P.thresh)) continue;
+    grad_add<N>(w * w, order, lt, act, m2, ga, gb);
+  }
+  grad_store<N>(m2, ga, gb, out);
+}
+
 // ---------------------------------------------------------------------------
 // per-graph kernel set
 // ---------------------------------------------------------------------------
 struct KernelSet {
-  const void *integrate, *redo, *dump, *eval, *grad;
+  const void *integrate, *redo, *dump, *eval, *grad, *grad_dd;
   int lines;
 };
 #define QED_DEFINE_KSET(id, lines)                                                              \
   extern const KernelSet qed_kset_##id;                                                        \
   const KernelSet qed_kset_##id = {(const void *)k_integrate<id, lines>, (const void *)k_redo_dd<id, lines>, \
                                    (const void *)k_dump<id, lines>, (const void *)k_eval<id, lines>,            \
-                                   (const void *)k_pdf_grad<id, lines>, lines};
+                                   (const void *)k_pdf_grad<id, lines>, (const void *)k_pdf_grad_dd<id, lines>, \
+                                   lines};

@@ -440,6 +440,8 @@ __global__ void __launch_bounds__(256) k_eval_vm(const double *__restrict__ zin,
 
 // Adjoint of the second moment over recomputed samples (same sums as
 // k_pdf_grad; the integrand is the program).  out: [gridDim.x][2N + 1].
+// Adjoint sums of the second moment (see k_pdf_grad): points whose FP64
+// estimate fails the threshold are queued for k_pdf_grad_dd_vm.
 template <int N, int P>
 __global__ void __launch_bounds__(256) k_pdf_grad_vm(KParams K, VmCode C, const uint8_t *__restrict__ act, double *out) {
   extern __shared__ __align__(16) unsigned char vsm[];
@@ -460,44 +462,46 @@ __global__ void __launch_bounds__(256) k_pdf_grad_vm(KParams K, VmCode C, const 
     fr.template eval<N>(C, z, f, ab);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-      if (i0 + p * nth >= K.n) continue;
-      double w = f[p] * exp(-lp[p]);
-      if (!isfinite(w)) w = 0.0;
-      const double w2 = w * w;
-      m2 += w2;
-      double cum = 0.0;
-      uint32_t S = (1u << N) - 1u;
-#pragma unroll
-      for (int r = 0; r < N; ++r) {
-        if (r > 0) {
-          S &= ~(1u << order[p][r - 1]);
-          if (act[S]) cum += lt[p][r];
-        }
-#pragma unroll
-        for (int m = 0; m < N; ++m) if (order[p][r] == m) ga[m] += w2 * cum;
+      const uint64_t i = i0 + p * nth;
+      if (i >= K.n) continue;
+      const double w = f[p] * exp(-lp[p]);
+      if (!isfinite(w) || !(rel_err_estimate(f[p], ab[p], 1.1102230246251565e-16) <= K.thresh)) {
+        const unsigned int slot = atomicAdd(K.queue_len, 1u);
+        if (slot < K.queue_cap) K.queue[slot] = i;
+        continue;
       }
-#pragma unroll
-      for (int m = 0; m < N; ++m) if (order[p][0] == m) gb[m] += w2;
+      grad_add<N>(w * w, order[p], lt[p], act, m2, ga, gb);
     }
   }
-  __shared__ double red[8][2 * N + 1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double v[2 * N + 1];
-  v[0] = m2;
+  grad_store<N>(m2, ga, gb, out);
+}
+
+// The queued points of k_pdf_grad_vm in double-double; a point that fails
+// the threshold there too contributes w = 0, as in the estimator.
+template <int N>
+__global__ void __launch_bounds__(256) k_pdf_grad_dd_vm(KParams K, VmCode C, unsigned int qn,
+                                                        const uint8_t *__restrict__ act, double *out) {
+  extern __shared__ __align__(16) unsigned char vsm[];
+  VmFrame<dd, 1> fr;
+  fr.setup(C, vsm);
+  double m2 = 0.0, ga[N], gb[N];
 #pragma unroll
-  for (int m = 0; m < N; ++m) { v[1 + m] = ga[m]; v[1 + N + m] = gb[m]; }
+  for (int m = 0; m < N; ++m) { ga[m] = 0.0; gb[m] = 0.0; }
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < qn; i += stride) {
+    double z[N], lt[N];
+    int order[N];
+    const double lp = draw_point<N, true>(K.begin + K.queue[i], K, K.F, K.G, K.invdeg, z, order, lt);
+    dd zd[1][N], f[1];
+    double ab[1];
 #pragma unroll
-  for (int k = 0; k < 2 * N + 1; ++k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    if (lane == 0) red[warp][k] = v[k];
+    for (int L = 0; L < N; ++L) zd[0][L] = dd{z[L], 0.0};
+    fr.template eval<N>(C, zd, f, ab);
+    const double w = (f[0].hi + f[0].lo) * exp(-lp);
+    if (!isfinite(w) || !(rel_err_estimate(f[0].hi, ab[0], 1.2325951644078309e-32) <= K.thresh)) continue;
+    grad_add<N>(w * w, order, lt, act, m2, ga, gb);
   }
-  __syncthreads();
-  if (threadIdx.x < 2 * N + 1) {
-    double acc = 0.0;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) acc += red[w][threadIdx.x];
-    out[size_t(blockIdx.x) * (2 * N + 1) + threadIdx.x] = acc;
-  }
+  grad_store<N>(m2, ga, gb, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -623,9 +627,10 @@ __global__ void __launch_bounds__(256) k_batch_vm_dd(BatchParams B) {
 // Kernel table of the bytecode path for one line count N and P points per
 // thread in the FP64 kernels.
 struct VmKernelSet {
-  const void *integrate, *redo, *dump, *eval, *grad, *batch64, *batchdd;
+  const void *integrate, *redo, *dump, *eval, *grad, *batch64, *batchdd, *grad_dd;
 };
 #define QED_VM_KSET(N, P)                                                                                       \
   VmKernelSet{(const void *)k_integrate_vm<N, P>, (const void *)k_redo_dd_vm<N>, (const void *)k_dump_vm<N, P>, \
               (const void *)k_eval_vm<N, P>, (const void *)k_pdf_grad_vm<N, P>,                                 \
-              (const void *)k_batch_vm_fp64<N, P>, (const void *)k_batch_vm_dd<N>}
+              (const void *)k_batch_vm_fp64<N, P>, (const void *)k_batch_vm_dd<N>,                              \
+              (const void *)k_pdf_grad_dd_vm<N>}

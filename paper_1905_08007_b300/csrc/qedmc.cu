@@ -75,7 +75,7 @@ struct qed_ctx {
   unsigned int *queue_len = nullptr;
   unsigned int queue_cap = 1u << 22;
   int partial_cap = 0;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk0 = nullptr, evk1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk0 = nullptr, evk1 = nullptr, evk2 = nullptr;
   std::vector<double> h_partials;
   std::vector<unsigned long long> h_counts;
   // bytecode integrands registered by qed_programs_load
@@ -83,12 +83,14 @@ struct qed_ctx {
     std::string name;
     int n_lines, n_regs, n_ins, n_kon;
     double flops;
+    double dd_flops;        // FP64 operations of one double-double evaluation
     const uint2 *d_ins;
     const double *d_kon;
   };
   std::vector<VmProg> vm;
   std::vector<void *> vm_bufs;
   bool prefer_vm = false;
+  struct BatchPlan *plan = nullptr;   // qed_integrate_batch's cached set-up
   int vm_threads = 128;      // threads per block of the FP64 interpreter kernels
   int vm_points = 1;         // points per thread of the FP64 interpreter kernels
 };
@@ -188,15 +190,18 @@ extern "C" int qed_ctx_create(int device, uint64_t flags, qed_ctx **out) {
   CUDA_TRY(cudaEventCreate(&c->ev1));
   CUDA_TRY(cudaEventCreate(&c->evk0));
   CUDA_TRY(cudaEventCreate(&c->evk1));
+  CUDA_TRY(cudaEventCreate(&c->evk2));
   int rc = ensure_scratch(c, 8 * c->sms);
   if (rc) return rc;
   *out = c;
   return QED_OK;
 }
 
+static void drop_plan(qed_ctx *c);
 extern "C" int qed_ctx_destroy(qed_ctx *c) {
   if (!c) return QED_OK;
   cudaSetDevice(c->device);
+  drop_plan(c);
   if (c->partials) cudaFree(c->partials);
   if (c->counts) cudaFree(c->counts);
   if (c->queue) cudaFree(c->queue);
@@ -205,6 +210,7 @@ extern "C" int qed_ctx_destroy(qed_ctx *c) {
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->evk0) cudaEventDestroy(c->evk0);
   if (c->evk1) cudaEventDestroy(c->evk1);
+  if (c->evk2) cudaEventDestroy(c->evk2);
   for (void *p : c->vm_bufs) cudaFree(p);
   delete c;
   return QED_OK;
@@ -271,6 +277,33 @@ static bool vm_check(const uint2 *ins, int n_ins, int n_regs, int n_kon, int n_l
   return false;
 }
 
+// FP64 operations (an FMA counts 2) of one evaluation of a program in the
+// interpreter's double-double arithmetic, instruction by instruction: the
+// fused step acc = X * B + O costs 18 in general, 10 without an addend, 11
+// when B is the constant 1 and there is an addend, none for a move; its
+// absolute-value lane one FMA; RCP a double-double division (86); ACCW one
+// FMA.  An algorithmic count of the re-evaluation of a flagged point.
+static double vm_dd_flops(const uint2 *ins, int n_ins, const unsigned char *kon, int n_kon) {
+  double f = 0.0;
+  for (int i = 0; i < n_ins; ++i) {
+    const uint32_t lo = ins[i].x, hi = ins[i].y;
+    const uint32_t b = (lo >> 13) & 8191u, zo = (hi >> 1) & 1u, spec = (hi >> 2) & 7u, nocomp = (hi >> 5) & 1u;
+    if (!nocomp) {
+      bool b_one = false;
+      if (b >= 4096u && int(b - 4096u) < n_kon) {
+        double v;
+        std::memcpy(&v, kon + 8 * size_t(b - 4096u), 8);
+        b_one = v == 1.0;
+      }
+      f += b_one ? (zo ? 11.0 : 0.0) : (zo ? 18.0 : 10.0);
+      f += 2.0;
+    }
+    if (spec == 1u) f += 86.0;
+    else if (spec == 3u) f += 2.0;
+  }
+  return f;
+}
+
 extern "C" int qed_programs_load(qed_ctx *c, const void *data, size_t bytes, int *count) {
   if (!c || !data) return set_err(QED_EINVAL, "ctx/data is NULL");
   const unsigned char *p = static_cast<const unsigned char *>(data), *end = p + bytes;
@@ -301,6 +334,7 @@ extern "C" int qed_programs_load(qed_ctx *c, const void *data, size_t bytes, int
     std::vector<uint2> tmp(static_cast<size_t>(m[2]));
     std::memcpy(tmp.data(), r.ins, ib);
     if (!vm_check(tmp.data(), m[2], m[1], m[3], m[0], why)) return set_err(QED_EINVAL, "program " + r.pr.name + ": " + why);
+    r.pr.dd_flops = vm_dd_flops(tmp.data(), m[2], r.kon, m[3]);
     p += ib + kb;
     words += (((size_t(m[2]) + 1) & ~size_t(1)) + 16) * 2;  // 32-bit words: pairs, plus 8 zero groups
     kons += size_t(m[3]);
@@ -555,9 +589,14 @@ static int integrate_range_vm(qed_diag *d, uint64_t begin, uint64_t n, uint64_t 
     if (qn > c->queue_cap) return set_err(QED_ECUDA, "flagged queue overflow");   // cannot happen: m <= queue_cap
     if (qn > 0) {
       void *args2[] = {&P, &L2.code, &qn};
+      CUDA_TRY(cudaEventRecord(c->evk1, c->stream));
       if ((rc = launch(K.redo, L2.blocks, L2.threads, L2.smem, c->stream, args2))) return rc;
+      CUDA_TRY(cudaEventRecord(c->evk2, c->stream));
       ++r.launches;
       if ((rc = fold(c, L2.blocks, &r, false))) return rc;
+      float dms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&dms, c->evk1, c->evk2));
+      r.dd_seconds += dms * 1e-3;
     }
   }
   CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
@@ -629,19 +668,34 @@ extern "C" int qed_integrate_range(qed_diag *d, uint64_t begin, uint64_t n, uint
     if ((rc = launch(K.integrate, blocks, threads, smem, c->stream, args))) return rc;
     CUDA_TRY(cudaEventRecord(c->evk1, c->stream));
     ++r.launches;
-    if ((rc = fold(c, blocks, &r, true))) return rc;
+    qed_result first;
+    std::memset(&first, 0, sizeof first);
+    if ((rc = fold(c, blocks, &first, true))) return rc;
     float kms = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&kms, c->evk0, c->evk1));
     r.kernel_seconds += kms * 1e-3;
     unsigned int qn = 0;
     CUDA_TRY(cudaMemcpy(&qn, c->queue_len, sizeof qn, cudaMemcpyDeviceToHost));
+    // mode 1 (the queue overflowed): the double-double kernel makes a
+    // complete second pass that replaces this one (flag decisions included)
+    const int mode = qn > c->queue_cap ? 1 : 0;
+    if (mode == 0) {
+      dd_acc(r.sum_w[0], r.sum_w[1], first.sum_w[0], first.sum_w[1]);
+      dd_acc(r.sum_w2[0], r.sum_w2[1], first.sum_w2[0], first.sum_w2[1]);
+      r.n_flagged += first.n_flagged;
+    }
     if (qn > 0) {
-      int mode = qn > c->queue_cap ? 1 : 0;
+      int m = mode;
       unsigned int qcount = std::min(qn, c->queue_cap);
-      void *args2[] = {&P, &mode, &qcount};
+      void *args2[] = {&P, &m, &qcount};
+      CUDA_TRY(cudaEventRecord(c->evk1, c->stream));
       if ((rc = launch(K.redo, blocks, threads, smem, c->stream, args2))) return rc;
+      CUDA_TRY(cudaEventRecord(c->evk2, c->stream));
       ++r.launches;
-      if ((rc = fold(c, blocks, &r, false))) return rc;
+      if ((rc = fold(c, blocks, &r, mode == 1))) return rc;
+      float dms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&dms, c->evk1, c->evk2));
+      r.dd_seconds += dms * 1e-3;
     }
   }
   CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
@@ -720,6 +774,7 @@ extern "C" int qed_result_merge(const qed_result *a, const qed_result *b, qed_re
   r.n_flagged = a->n_flagged + b->n_flagged;
   r.n_unstable = a->n_unstable + b->n_unstable;
   r.seconds = a->seconds + b->seconds;
+  r.dd_seconds = a->dd_seconds + b->dd_seconds;
   r.kernel_seconds = a->kernel_seconds + b->kernel_seconds;
   r.launches = a->launches + b->launches;
   finish(&r);
@@ -754,6 +809,24 @@ __global__ void k_fp64_peak(double *out, int iters, double b, double c) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) s += a[i];
   if (s == -1.2345e300) out[0] = s;   // keeps the chains live
+}
+
+extern "C" int qed_diagram_flops_dd(const qed_diag *d, double *flops) {
+  if (!d || !flops) return set_err(QED_EINVAL, "NULL argument");
+  const qed_ctx *c = d->ctx;
+  int k = d->vm;
+  if (k < 0) {
+    // compiled integrand: the count of the same graph's program, if registered
+    const std::string nm = d->g.name();
+    for (size_t i = 0; i < c->vm.size() && k < 0; ++i)
+      if (c->vm[i].name == nm) k = int(i);
+    if (k < 0) return set_err(QED_ENOTFOUND, "no program of this graph is registered (qed_programs_load)");
+  }
+  double f64 = 0.0;
+  qed_diagram_flops(d, &f64);
+  // the sampler part runs in FP64 in both passes
+  *flops = c->vm[k].dd_flops + (f64 - (d->vm >= 0 ? c->vm[d->vm].flops : qed_generated_flops[d->fid]));
+  return QED_OK;
 }
 
 extern "C" int qed_fp64_peak(int device, double ms, double *flops) {
@@ -792,16 +865,120 @@ extern "C" int qed_fp64_peak(int device, double ms, double *flops) {
 // batched integration of a graph set (persistent kernel, variance-driven
 // allocation, one CUDA graph per round shape replayed every round)
 // ---------------------------------------------------------------------------
-namespace {
-struct DevBuf {
-  void *p = nullptr;
-  ~DevBuf() { if (p) cudaFree(p); }
+// qed_integrate_batch's set-up: device buffers, pinned host buffers and the
+// captured round (a CUDA graph), owned by the context and reused by the next
+// call of the same shape (same graphs, seed, threshold, item count, list
+// size, kernels and launch shapes, stream), so that a caller integrating the
+// same set step after step pays for the allocations and the capture once.
+struct BatchPlan {
+  // shape (the key)
+  std::vector<qed_diag *> diags;
+  uint64_t seed = 0;
+  double thresh = 0.0;
+  unsigned int n_items = 0;
+  uint32_t list_cap = 0, dd_tiles = 0;
+  const void *kern1 = nullptr, *kern2 = nullptr;
+  int grid1 = 0, grid2 = 0, thr1 = 0, thr2 = 0;
+  size_t smem = 0, smem2 = 0;
+  bool use_graph = true;
+  cudaStream_t user_stream = 0;
+  // resources: dev = {graph descriptors, items, next-item counters, FP64
+  // partials, FP64 counts, dd partials, dd counts, flagged lists}
+  void *dev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  void *h_items = nullptr, *h_out = nullptr;
+  double *o_part = nullptr, *o_pdd = nullptr;
+  unsigned long long *o_cnt = nullptr, *o_cdd = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t st = 0;
+  bool own_stream = false;
+  BatchParams B;
+  size_t n_dd = 0;
+
+  bool same_shape(const BatchPlan &o) const {
+    return diags == o.diags && seed == o.seed && thresh == o.thresh && n_items == o.n_items &&
+           list_cap == o.list_cap && dd_tiles == o.dd_tiles && kern1 == o.kern1 && kern2 == o.kern2 &&
+           grid1 == o.grid1 && grid2 == o.grid2 && thr1 == o.thr1 && thr2 == o.thr2 && smem == o.smem &&
+           smem2 == o.smem2 && use_graph == o.use_graph && user_stream == o.user_stream;
+  }
+  BatchPlan() = default;
+  BatchPlan(const BatchPlan &key) : diags(key.diags), seed(key.seed), thresh(key.thresh), n_items(key.n_items),
+      list_cap(key.list_cap), dd_tiles(key.dd_tiles), kern1(key.kern1), kern2(key.kern2), grid1(key.grid1),
+      grid2(key.grid2), thr1(key.thr1), thr2(key.thr2), smem(key.smem), smem2(key.smem2),
+      use_graph(key.use_graph), user_stream(key.user_stream) {}
+  BatchPlan &operator=(const BatchPlan &) = delete;
+  ~BatchPlan() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (own_stream && st) cudaStreamDestroy(st);
+    for (void *p : dev) if (p) cudaFree(p);
+    if (h_items) cudaFreeHost(h_items);
+    if (h_out) cudaFreeHost(h_out);
+  }
+
+  // copy the items in, run the FP64 kernel and the double-double kernel,
+  // copy the partials out; with external event nodes when captured, so the
+  // kernels can be timed after every replay
+  int enqueue_round(qed_ctx *c, cudaStream_t s, bool capturing) {
+    CUDA_TRY(cudaMemcpyAsync(dev[1], h_items, sizeof(BatchItem) * n_items, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(dev[2], 0, 2 * sizeof(unsigned int), s));
+    void *args[] = {&B};
+    const unsigned int evflags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    CUDA_TRY(cudaEventRecordWithFlags(c->evk0, s, evflags));
+    CUDA_TRY(cudaLaunchKernel(kern1, dim3(grid1), dim3(thr1), args, smem, s));
+    CUDA_TRY(cudaEventRecordWithFlags(c->evk1, s, evflags));
+    CUDA_TRY(cudaLaunchKernel(kern2, dim3(grid2), dim3(thr2), args, smem2, s));
+    CUDA_TRY(cudaEventRecordWithFlags(c->evk2, s, evflags));
+    CUDA_TRY(cudaMemcpyAsync(o_part, dev[3], sizeof(double) * 4 * n_items, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(o_pdd, dev[5], sizeof(double) * 4 * n_dd, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(o_cnt, dev[4], sizeof(unsigned long long) * 2 * n_items, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(o_cdd, dev[6], sizeof(unsigned long long) * 2 * n_dd, cudaMemcpyDeviceToHost, s));
+    return QED_OK;
+  }
+
+  int allocate(qed_ctx *c, int k, size_t ndd) {
+    n_dd = ndd;
+    CUDA_TRY(cudaMalloc(&dev[0], sizeof(BatchDiag) * k));
+    CUDA_TRY(cudaMalloc(&dev[1], sizeof(BatchItem) * n_items));
+    CUDA_TRY(cudaMalloc(&dev[2], 2 * sizeof(unsigned int)));
+    CUDA_TRY(cudaMalloc(&dev[3], sizeof(double) * 4 * n_items));
+    CUDA_TRY(cudaMalloc(&dev[4], sizeof(unsigned long long) * 2 * n_items));
+    CUDA_TRY(cudaMalloc(&dev[5], sizeof(double) * 4 * n_dd));
+    CUDA_TRY(cudaMalloc(&dev[6], sizeof(unsigned long long) * 2 * n_dd));
+    CUDA_TRY(cudaMalloc(&dev[7], sizeof(uint32_t) * size_t(list_cap) * n_items));
+    const size_t out_bytes = n_items * (4 * sizeof(double) + 2 * sizeof(unsigned long long)) +
+                             n_dd * (4 * sizeof(double) + 2 * sizeof(unsigned long long));
+    CUDA_TRY(cudaMallocHost(&h_items, sizeof(BatchItem) * n_items));
+    CUDA_TRY(cudaMallocHost(&h_out, out_bytes));
+    o_part = (double *)h_out;
+    o_pdd = o_part + 4 * size_t(n_items);
+    o_cnt = (unsigned long long *)(o_pdd + 4 * n_dd);
+    o_cdd = o_cnt + 2 * size_t(n_items);
+    B.diags = (const BatchDiag *)dev[0]; B.items = (const BatchItem *)dev[1]; B.n_items = n_items;
+    B.next_item = (unsigned int *)dev[2]; B.key0 = uint32_t(seed); B.key1 = uint32_t(seed >> 32);
+    B.thresh = thresh; B.part = (double *)dev[3]; B.cnt = (unsigned long long *)dev[4];
+    B.lists = (uint32_t *)dev[7]; B.list_cap = list_cap;
+    B.part_dd = (double *)dev[5]; B.cnt_dd = (unsigned long long *)dev[6];
+    B.dd_tiles = dd_tiles; B.next_tile = (unsigned int *)dev[2] + 1;
+    st = user_stream;
+    if (use_graph) {
+      if (st == 0) { CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own_stream = true; }
+      cudaGraph_t graph;
+      CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      int rc = enqueue_round(c, st, true);
+      cudaError_t ce = cudaStreamEndCapture(st, &graph);
+      if (rc) return rc;
+      if (ce != cudaSuccess) return set_err(QED_ECUDA, std::string("capture: ") + cudaGetErrorString(ce));
+      ce = cudaGraphInstantiate(&gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) return set_err(QED_ECUDA, std::string("instantiate: ") + cudaGetErrorString(ce));
+    }
+    return QED_OK;
+  }
 };
-struct HostBuf {
-  void *p = nullptr;
-  ~HostBuf() { if (p) cudaFreeHost(p); }
-};
-}  // namespace
+
+static void drop_plan(qed_ctx *c) {
+  delete c->plan;
+  c->plan = nullptr;
+}
 
 extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64_t total, uint64_t seed,
                                    const qed_batch_opts *opts, qed_result *out) {
@@ -850,24 +1027,28 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
     if (rc) return rc;
     smem = L1.smem; smem2 = L2.smem; thr1 = L1.threads; thr2 = L2.threads;
   }
-  // device and pinned buffers
-  DevBuf dd_diags, dd_items, dd_next, dd_part, dd_cnt, dd_lists, dd_pdd, dd_cdd;
   // bytecode batches: the dd pass runs in tiles of one point per thread
   const uint32_t dd_tiles = vmb ? uint32_t((chunk + uint64_t(thr2) - 1) / uint64_t(thr2)) : 1u;
   const size_t n_dd = size_t(n_items) * dd_tiles;
-  HostBuf h_items, h_out;
-  CUDA_TRY(cudaMalloc(&dd_diags.p, sizeof(BatchDiag) * k));
-  CUDA_TRY(cudaMalloc(&dd_items.p, sizeof(BatchItem) * n_items));
-  CUDA_TRY(cudaMalloc(&dd_next.p, 2 * sizeof(unsigned int)));
-  CUDA_TRY(cudaMalloc(&dd_part.p, sizeof(double) * 4 * n_items));
-  CUDA_TRY(cudaMalloc(&dd_cnt.p, sizeof(unsigned long long) * 2 * n_items));
-  CUDA_TRY(cudaMalloc(&dd_pdd.p, sizeof(double) * 4 * n_dd));
-  CUDA_TRY(cudaMalloc(&dd_cdd.p, sizeof(unsigned long long) * 2 * n_dd));
-  CUDA_TRY(cudaMalloc(&dd_lists.p, sizeof(uint32_t) * size_t(list_cap) * n_items));
-  const size_t out_bytes = n_items * (4 * sizeof(double) + 2 * sizeof(unsigned long long)) +
-                           n_dd * (4 * sizeof(double) + 2 * sizeof(unsigned long long));
-  CUDA_TRY(cudaMallocHost(&h_items.p, sizeof(BatchItem) * n_items));
-  CUDA_TRY(cudaMallocHost(&h_out.p, out_bytes));
+  int occ = 0;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern1, thr1, smem));
+  const int grid1 = std::max(1, occ) * c->sms;
+  const int grid2 = vmb ? int(std::min<size_t>(n_dd, size_t(L2.blocks))) : std::min<int>(int(n_items), 4 * c->sms);
+  // the set-up (buffers, pinned memory, the captured round) is kept on the
+  // context and reused while the batch's shape is the same
+  BatchPlan key;
+  key.diags.assign(d, d + k);
+  key.seed = seed; key.thresh = c->thresh; key.n_items = n_items; key.list_cap = list_cap; key.dd_tiles = dd_tiles;
+  key.kern1 = kern1; key.kern2 = kern2; key.grid1 = grid1; key.grid2 = grid2; key.thr1 = thr1; key.thr2 = thr2;
+  key.smem = smem; key.smem2 = smem2; key.use_graph = o.use_graph >= 0; key.user_stream = c->stream;
+  if (!c->plan || !c->plan->same_shape(key)) {
+    drop_plan(c);
+    BatchPlan *P = new BatchPlan(key);
+    c->plan = P;
+    int rc = P->allocate(c, k, n_dd);
+    if (rc) { drop_plan(c); return rc; }
+  }
+  BatchPlan &PL = *c->plan;
   std::vector<BatchDiag> hd(k);
   for (int g = 0; g < k; ++g) {
     const size_t M = size_t(1) << d[g]->N;
@@ -879,64 +1060,22 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
       hd[g].vins = pr.d_ins; hd[g].vkon = pr.d_kon; hd[g].vnk = pr.n_kon; hd[g].vnr = pr.n_regs;
     }
   }
-  CUDA_TRY(cudaMemcpy(dd_diags.p, hd.data(), sizeof(BatchDiag) * k, cudaMemcpyHostToDevice));
-  BatchParams B;
-  B.diags = (const BatchDiag *)dd_diags.p; B.items = (const BatchItem *)dd_items.p; B.n_items = n_items;
-  B.next_item = (unsigned int *)dd_next.p; B.key0 = uint32_t(seed); B.key1 = uint32_t(seed >> 32);
-  B.thresh = c->thresh; B.part = (double *)dd_part.p; B.cnt = (unsigned long long *)dd_cnt.p;
-  B.lists = (uint32_t *)dd_lists.p; B.list_cap = list_cap;
-  B.part_dd = (double *)dd_pdd.p; B.cnt_dd = (unsigned long long *)dd_cdd.p;
-  B.dd_tiles = dd_tiles; B.next_tile = (unsigned int *)dd_next.p + 1;
-  int occ = 0;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern1, thr1, smem));
-  const int grid1 = std::max(1, occ) * c->sms;
-  const int grid2 = vmb ? int(std::min<size_t>(n_dd, size_t(L2.blocks))) : std::min<int>(int(n_items), 4 * c->sms);
-  // host-side layout of the pinned output block
-  double *o_part = (double *)h_out.p;
-  double *o_pdd = o_part + 4 * size_t(n_items);
-  unsigned long long *o_cnt = (unsigned long long *)(o_pdd + 4 * n_dd);
-  unsigned long long *o_cdd = o_cnt + 2 * size_t(n_items);
-  auto enqueue_round = [&](cudaStream_t st, bool capturing) -> int {
-    CUDA_TRY(cudaMemcpyAsync(dd_items.p, h_items.p, sizeof(BatchItem) * n_items, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemsetAsync(dd_next.p, 0, 2 * sizeof(unsigned int), st));
-    void *args[] = {&B};
-    // external event-record nodes when captured, so the kernel can be timed
-    // after every replay
-    const unsigned int evflags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-    CUDA_TRY(cudaEventRecordWithFlags(c->evk0, st, evflags));
-    CUDA_TRY(cudaLaunchKernel(kern1, dim3(grid1), dim3(thr1), args, smem, st));
-    CUDA_TRY(cudaEventRecordWithFlags(c->evk1, st, evflags));
-    CUDA_TRY(cudaLaunchKernel(kern2, dim3(grid2), dim3(thr2), args, smem2, st));
-    CUDA_TRY(cudaMemcpyAsync(o_part, dd_part.p, sizeof(double) * 4 * n_items, cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaMemcpyAsync(o_pdd, dd_pdd.p, sizeof(double) * 4 * n_dd, cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaMemcpyAsync(o_cnt, dd_cnt.p, sizeof(unsigned long long) * 2 * n_items, cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaMemcpyAsync(o_cdd, dd_cdd.p, sizeof(unsigned long long) * 2 * n_dd, cudaMemcpyDeviceToHost, st));
-    return QED_OK;
-  };
-  cudaGraphExec_t gexec = nullptr;
-  cudaStream_t st = c->stream;
-  bool own_stream = false;
-  if (o.use_graph >= 0) {
-    if (st == 0) { CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own_stream = true; }
-    cudaGraph_t graph;
-    CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_round(st, true);
-    cudaError_t ce = cudaStreamEndCapture(st, &graph);
-    if (rc) return rc;
-    if (ce != cudaSuccess) return set_err(QED_ECUDA, std::string("capture: ") + cudaGetErrorString(ce));
-    ce = cudaGraphInstantiate(&gexec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) return set_err(QED_ECUDA, std::string("instantiate: ") + cudaGetErrorString(ce));
-  }
+  // the graphs' tables may have been rebuilt since the last call: upload
+  // their descriptors every time (a few hundred bytes, before the rounds)
+  CUDA_TRY(cudaMemcpy(PL.dev[0], hd.data(), sizeof(BatchDiag) * k, cudaMemcpyHostToDevice));
+  double *o_part = PL.o_part, *o_pdd = PL.o_pdd;
+  unsigned long long *o_cnt = PL.o_cnt, *o_cdd = PL.o_cdd;
+  cudaGraphExec_t gexec = PL.gexec;
+  cudaStream_t st = PL.st;
   // per-graph running state
   std::vector<qed_result> R(k);
   std::vector<uint64_t> next(k, o.counter_base);
   for (int g = 0; g < k; ++g) std::memset(&R[g], 0, sizeof(qed_result));
   std::vector<double> weight(k, 1.0), cost(k, 0.0);
   for (int g = 0; g < k; ++g) qed_diagram_flops(d[g], &cost[g]);
-  BatchItem *hi = (BatchItem *)h_items.p;
+  BatchItem *hi = (BatchItem *)PL.h_items;
   uint32_t launches = 0;
-  double kernel_ms = 0.0;
+  double kernel_ms = 0.0, dd_ms = 0.0;
   CUDA_TRY(cudaEventRecord(c->ev0, st));
   for (int r = 0; r < rounds; ++r) {
     // split n_items among graphs: round 0 (and policy 1) equal, else by weight
@@ -976,13 +1115,15 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
         ++it;
       }
     if (gexec) { CUDA_TRY(cudaGraphLaunch(gexec, st)); }
-    else { int rc = enqueue_round(st, false); if (rc) return rc; }
+    else { int rc = PL.enqueue_round(c, st, false); if (rc) return rc; }
     launches += 2;
     CUDA_TRY(cudaStreamSynchronize(st));
     {
       float kms = 0.f;
       if (cudaEventElapsedTime(&kms, c->evk0, c->evk1) == cudaSuccess) kernel_ms += kms;
       else (void)cudaGetLastError();   // timing unavailable: leave no error behind
+      if (cudaEventElapsedTime(&kms, c->evk1, c->evk2) == cudaSuccess) dd_ms += kms;
+      else (void)cudaGetLastError();
     }
     for (unsigned int i = 0; i < n_items; ++i) {
       qed_result &q = R[hi[i].diag];
@@ -1014,12 +1155,11 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
   CUDA_TRY(cudaEventSynchronize(c->ev1));
   float ms = 0.f;
   CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-  if (gexec) cudaGraphExecDestroy(gexec);
-  if (own_stream) cudaStreamDestroy(st);
   for (int g = 0; g < k; ++g) {
     finish(&R[g]);
     R[g].seconds = ms * 1e-3;
     R[g].kernel_seconds = kernel_ms * 1e-3;
+    R[g].dd_seconds = dd_ms * 1e-3;
     R[g].launches = launches;
     out[g] = R[g];
   }
@@ -1076,34 +1216,56 @@ extern "C" int qed_pdf_grad(qed_diag *d, uint64_t begin, uint64_t n, uint64_t se
   if (!d || !m2 || !grad || n == 0) return set_err(QED_EINVAL, "bad argument");
   qed_ctx *c = d->ctx;
   CUDA_TRY(cudaSetDevice(c->device));
-  const int N = d->N;
-  int blocks = 4 * c->sms, threads = 256;
-  VmLaunch L;
-  if (d->vm >= 0) {
+  const int N = d->N, W = 2 * N + 1;
+  const bool vm = d->vm >= 0;
+  // FP64 pass (flagged points queued) and double-double pass over the queue
+  int blocks = 4 * c->sms, threads = 256, blocks2 = blocks, threads2 = threads;
+  size_t smem = table_smem(N), smem2 = smem;
+  VmLaunch L, L2;
+  if (vm) {
     int rc = vm_launch(c, c->vm[d->vm], vm_kernels(d).grad, false, c->vm_threads, L);
+    if (!rc) rc = vm_launch(c, c->vm[d->vm], vm_kernels(d).grad_dd, true, 64, L2);
     if (rc) return rc;
-    blocks = L.blocks;
-    threads = L.threads;
+    blocks = L.blocks; threads = L.threads; smem = L.smem;
+    blocks2 = L2.blocks; threads2 = L2.threads; smem2 = L2.smem;
   }
+  const int B = std::max(blocks, blocks2);
   double *dout = nullptr;
-  CUDA_TRY(cudaMalloc(&dout, sizeof(double) * blocks * (2 * N + 1)));
-  KParams P = base_params(d, begin, n, seed);
+  CUDA_TRY(cudaMalloc(&dout, sizeof(double) * size_t(B) * W));
+  std::vector<double> h(size_t(B) * W), acc(W, 0.0);
   const uint8_t *act = d->d_act;
-  void *args[] = {&P, (void *)&act, &dout};
-  void *vargs[] = {&P, &L.code, (void *)&act, &dout};
-  int rc = d->vm >= 0 ? launch(vm_kernels(d).grad, blocks, threads, L.smem, c->stream, vargs)
-                      : launch(g_kernels[d->fid]->grad, blocks, threads, table_smem(N), c->stream, args);
-  std::vector<double> h(size_t(blocks) * (2 * N + 1));
-  if (!rc) {
-    cudaError_t e = cudaMemcpyAsync(h.data(), dout, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  auto collect = [&](int nb) -> int {
+    cudaError_t e = cudaMemcpyAsync(h.data(), dout, size_t(nb) * W * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) rc = set_err(QED_ECUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) return set_err(QED_ECUDA, cudaGetErrorString(e));
+    for (int b = 0; b < nb; ++b)
+      for (int k = 0; k < W; ++k) acc[k] += h[size_t(b) * W + k];
+    return QED_OK;
+  };
+  int rc = QED_OK;
+  // launches of at most queue_cap samples: the flagged queue cannot overflow
+  for (uint64_t off = 0; off < n && !rc; off += c->queue_cap) {
+    const uint64_t m = std::min<uint64_t>(c->queue_cap, n - off);
+    KParams P = base_params(d, begin + off, m, seed);
+    P.queue = c->queue; P.queue_len = c->queue_len; P.queue_cap = c->queue_cap;
+    if (cudaMemsetAsync(c->queue_len, 0, sizeof(unsigned int), c->stream) != cudaSuccess) { rc = set_err(QED_ECUDA, "memset"); break; }
+    void *args[] = {&P, (void *)&act, &dout};
+    void *vargs[] = {&P, &L.code, (void *)&act, &dout};
+    rc = vm ? launch(vm_kernels(d).grad, blocks, threads, smem, c->stream, vargs)
+            : launch(g_kernels[d->fid]->grad, blocks, threads, smem, c->stream, args);
+    if (!rc) rc = collect(blocks);
+    unsigned int qn = 0;
+    if (!rc && cudaMemcpy(&qn, c->queue_len, sizeof qn, cudaMemcpyDeviceToHost) != cudaSuccess) rc = set_err(QED_ECUDA, "copy");
+    if (!rc && qn > 0) {
+      void *args2[] = {&P, &qn, (void *)&act, &dout};
+      void *vargs2[] = {&P, &L2.code, &qn, (void *)&act, &dout};
+      rc = vm ? launch(vm_kernels(d).grad_dd, blocks2, threads2, smem2, c->stream, vargs2)
+              : launch(g_kernels[d->fid]->grad_dd, blocks2, threads2, smem2, c->stream, args2);
+      if (!rc) rc = collect(blocks2);
+    }
   }
   cudaFree(dout);
   if (rc) return rc;
-  std::vector<double> acc(2 * N + 1, 0.0);
-  for (int b = 0; b < blocks; ++b)
-    for (int k = 0; k < 2 * N + 1; ++k) acc[k] += h[size_t(b) * (2 * N + 1) + k];
   const double M2 = acc[0] / double(n);
   std::vector<double> ga, gb;
   dlogz(d, ga, gb);
@@ -1126,7 +1288,10 @@ extern "C" int qed_diagram_calibrate_deg(qed_diag *d, int n_base, uint64_t seed)
   qed_ctx *c = d->ctx;
   const int N = d->N;
   const size_t M = size_t(1) << N;
-  const double e1 = 1e-4, e2 = 1e-6;
+  // far enough into the limit that the integrand follows its power law: at
+  // 1e-4 .. 1e-5 some three-loop limits still show the bump of a nearby
+  // scale, from 1e-6 on the measured exponents are the asymptotic ones
+  const double e1 = 1e-6, e2 = 1e-8;
   // base points: uniform on the simplex (normalised exponentials)
   uint64_t st = seed * 0x9E3779B97F4A7C15ull + 0x2545F4914F6CDD1Dull;
   auto next = [&]() { st ^= st << 13; st ^= st >> 7; st ^= st << 17; return (double((st >> 11) + 1) * 1.1102230246251565e-16); };
@@ -1200,16 +1365,20 @@ struct NoAllocScratch {
   double result[8];                                       // folded sums (see k_noalloc_fold)
   unsigned int queue_len;
 };
-// Every GPU that loads the library holds this array (about 650 KB) until exit.
+static_assert(sizeof(NoAllocScratch) == 720968, "the header states this size");
+// Every GPU that loads the library holds this array (720,968 bytes, about
+// 704 KiB) from the moment the library's module is loaded on it until the
+// process exits.
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
-// Folds the per-block partials of both passes in block order, in
-// double-double: result = {sum w (hi, lo), sum w^2 (hi, lo), flagged, unstable}.
-__global__ void k_noalloc_fold(NoAllocScratch *s, int blocks, int with_dd) {
+// Folds the per-block partials of passes [p_begin, p_end) (0 = FP64, 1 =
+// double-double) in block order, in double-double: result = {sum w (hi, lo),
+// sum w^2 (hi, lo), flagged, unstable}.
+__global__ void k_noalloc_fold(NoAllocScratch *s, int blocks, int p_begin, int p_end) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   dd x{0.0, 0.0}, y{0.0, 0.0};
   unsigned long long nf = 0, nu = 0;
-  for (int p = 0; p < (with_dd ? 2 : 1); ++p)
+  for (int p = p_begin; p < p_end; ++p)
     for (int b = 0; b < blocks; ++b) {
       x = x + dd{s->part[p][b][0], s->part[p][b][1]};
       y = y + dd{s->part[p][b][2], s->part[p][b][3]};
@@ -1264,27 +1433,45 @@ extern "C" int qed_integrate_range_noalloc(qed_diag *d, uint64_t begin, uint64_t
     P.queue = S->queue; P.queue_len = &S->queue_len; P.queue_cap = QED_NOALLOC_QUEUE;
     CUDA_TRY(cudaMemsetAsync(&S->queue_len, 0, sizeof(unsigned int), c->stream));
     void *args[] = {&P};
+    CUDA_TRY(cudaEventRecord(c->evk0, c->stream));
     if ((rc = launch(K.integrate, blocks, threads, smem, c->stream, args))) return rc;
+    CUDA_TRY(cudaEventRecord(c->evk1, c->stream));
     ++r.launches;
     unsigned int qn = 0;
     CUDA_TRY(cudaMemcpyAsync(&qn, &S->queue_len, sizeof qn, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
-    int with_dd = 0;
+    float kms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&kms, c->evk0, c->evk1));
+    r.kernel_seconds += kms * 1e-3;
+    // passes to fold: the FP64 pass, plus the double-double pass over its
+    // queue; on overflow the double-double kernel re-scans the whole chunk
+    // and its pass alone replaces the first (one flag decision per point)
+    int p_begin = 0, p_end = 1;
+    bool dd_timed = false;
     if (qn > 0) {
-      int mode = qn > QED_NOALLOC_QUEUE ? 1 : 0;   // overflow: re-scan the range, no extra storage
+      int mode = qn > QED_NOALLOC_QUEUE ? 1 : 0;
       unsigned int qcount = std::min<unsigned int>(qn, QED_NOALLOC_QUEUE);
       KParams P2 = P;
       P2.partials = &S->part[1][0][0]; P2.counts = &S->cnt[1][0][0];
       void *args2[] = {&P2, &mode, &qcount};
+      CUDA_TRY(cudaEventRecord(c->evk1, c->stream));
       if ((rc = launch(K.redo, blocks, threads, smem, c->stream, args2))) return rc;
+      CUDA_TRY(cudaEventRecord(c->evk2, c->stream));
       ++r.launches;
-      with_dd = 1;
+      p_begin = mode;
+      p_end = 2;
+      dd_timed = true;
     }
-    void *args3[] = {&S, (void *)&blocks, &with_dd};
+    void *args3[] = {&S, (void *)&blocks, &p_begin, &p_end};
     if ((rc = launch((const void *)k_noalloc_fold, 1, 32, 0, c->stream, args3))) return rc;
     double res[6];
     CUDA_TRY(cudaMemcpyAsync(res, S->result, sizeof res, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (dd_timed) {
+      float dms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&dms, c->evk1, c->evk2));
+      r.dd_seconds += dms * 1e-3;
+    }
     dd_acc(r.sum_w[0], r.sum_w[1], res[0], res[1]);
     dd_acc(r.sum_w2[0], r.sum_w2[1], res[2], res[3]);
     r.n_flagged += (unsigned long long)res[4];

@@ -1,13 +1,18 @@
-"""Writes four_loop_points.txt: oracle values of four-loop integrands at the
-points that Eq. (1)'s sampler draws from given Philox counters (seed 0,
-stream id = the graph's index in the full enumeration).  Calls only oracle/.
+"""Writes four_loop_points.txt: oracle values of the four-loop integrands at
+the points that Eq. (1)'s sampler draws from given Philox counters (seed 0,
+stream id = the graph's index in the full enumeration, default Deg table).
+Calls only oracle/.
 
-    python tests/golden/make_four_loop.py
+    python tests/golden/make_four_loop.py [--procs 6]
 
-Graphs: one per forest-structure size in the mirror-reduced four-loop set
-(1, 3, 8, 16 and 46 forest terms).  Columns: graph index, counter, log p,
-z[0..11], f in long double (20 significant digits).
+Graphs: every mirror-reduced four-loop graph (269; Sec. 3 counts the
+mirror-reduced set), each at the counters in COUNTERS.  The oracle needs a few
+minutes per point, so rows are appended to four_loop_points.partial as they
+finish and a rerun resumes from it; the complete set is then written sorted.
+Columns: graph index, counter, log p, z[0..11], f in long double (20
+significant digits).
 """
+import argparse
 import multiprocessing as mp
 import sys
 from pathlib import Path
@@ -17,11 +22,20 @@ import numpy as np
 ROOT = Path(__file__).resolve().parents[2]
 sys.path.insert(0, str(ROOT))
 
-GRAPHS = [85, 113, 23, 442, 514]
-COUNTERS = [0, 1, 2, 3, 4, 5, 1_000_000_007]
+COUNTERS = [0, 1_000_000_007]
+OUT = Path(__file__).with_name("four_loop_points.txt")
+PARTIAL = Path(__file__).with_name("four_loop_points.partial")
 
 
-def rows(gi):
+def graphs():
+    from oracle.graphs import enumerate_graphs, enumerate_reduced
+    full = enumerate_graphs(4)
+    index = {g.key(): i for i, g in enumerate(full)}
+    return [index[g.key()] for g in enumerate_reduced(4)]
+
+
+def row(job):
+    gi, c = job
     from oracle.graphs import deg_table, enumerate_graphs
     from oracle.integrand import Integrand
     from oracle.pdf import f_table, sample_points
@@ -29,24 +43,40 @@ def rows(gi):
     g = enumerate_graphs(4)[gi]
     N = g.n_lines
     deg = deg_table(g)
-    u = uniforms(np.array(COUNTERS, dtype=np.uint64), gi, 0, 2 * (N - 1))
+    u = uniforms(np.array([c], dtype=np.uint64), gi, 0, 2 * (N - 1))
     x, lp, _ = sample_points(u, deg, f_table(deg, N), N)
     f = Integrand(g)(x, dtype=np.longdouble)
-    out = []
-    for k, c in enumerate(COUNTERS):
-        zs = " ".join(repr(float(v)) for v in x[k])
-        out.append(f"{gi} {c} {float(lp[k])!r} {zs} {np.format_float_scientific(f[k], precision=19)}")
-    return out
+    zs = " ".join(repr(float(v)) for v in x[0])
+    return f"{gi} {c} {float(lp[0])!r} {zs} {np.format_float_scientific(f[0], precision=19)}"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--procs", type=int, default=6)
+    a = ap.parse_args()
+    done = {}
+    if PARTIAL.exists():
+        for ln in PARTIAL.read_text().splitlines():
+            p = ln.split()
+            if len(p) == 16:
+                done[(int(p[0]), int(p[1]))] = ln
+    jobs = [(gi, c) for gi in graphs() for c in COUNTERS if (gi, c) not in done]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(a.procs) as pool, open(PARTIAL, "a") as fh:
+        for ln in pool.imap_unordered(row, jobs):
+            fh.write(ln + "\n")
+            fh.flush()
+            p = ln.split()
+            done[(int(p[0]), int(p[1]))] = ln
+    keys = sorted(done)
+    with open(OUT, "w") as fh:
+        fh.write("# four-loop integrand at Eq. (1) points (oracle, long double); written by make_four_loop.py\n")
+        fh.write("# graph counter logp z0..z11 f\n")
+        for k in keys:
+            fh.write(done[k] + "\n")
+    PARTIAL.unlink()
+    print(OUT, len(keys), "rows")
 
 
 if __name__ == "__main__":
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(len(GRAPHS)) as pool:
-        res = pool.map(rows, GRAPHS)
-    path = Path(__file__).with_name("four_loop_points.txt")
-    with open(path, "w") as fh:
-        fh.write("# four-loop integrand at Eq. (1) points (oracle, long double); written by make_four_loop.py\n")
-        fh.write("# graph counter logp z0..z11 f\n")
-        for r in res:
-            fh.write("\n".join(r) + "\n")
-    print(path)
+    main()

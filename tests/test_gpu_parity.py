@@ -73,7 +73,7 @@ def test_points_density_integrand_match_oracle(ctx, n, gi, begin, count):
     # double-double values of flagged points against the long-double oracle;
     # where the two disagree (the oracle's own V = sum z - sum z A^2 cancels
     # at IR corners, even in long double) the arbiter is the oracle in
-    # arbitrary precision (mpmath, 34 digits) on the four worst points
+    # arbitrary precision (mpmath, 34 digits) on every such point
     sub = np.arange(0, count, 5)
     fld = Integrand(og)(z[sub], dtype=np.longdouble).astype(np.float64)
     zt = torch.tensor(z[sub], dtype=torch.float64, device="cuda")
@@ -83,18 +83,28 @@ def test_points_density_integrand_match_oracle(ctx, n, gi, begin, count):
     _arbitrate(og, z[sub], gpu, rel)
 
 
-def _arbitrate(og, zs, gpu, rel, n_check=4, tol=1e-12):
+def _arbitrate(og, zs, gpu, rel, tol=1e-12, cap=64):
+    """Every point where the GPU value and the long-double oracle differ by
+    more than tol is settled by the oracle in 34-digit mpmath (the long-double
+    oracle loses digits of its own where its V = sum z - sum z A^2 cancels).
+    More than ``cap`` such points fail outright.  Returns (points settled by
+    mpmath, largest verified relative error)."""
     import mpmath
-    idx = np.argsort(-rel)[:n_check]
-    idx = [i for i in idx if rel[i] > tol]
-    if not idx:
-        return
+    idx = np.nonzero(rel > tol)[0]
+    assert len(idx) <= cap, f"{len(idx)} points above {tol} against the long-double oracle"
+    worst = float(np.max(rel[rel <= tol])) if np.any(rel <= tol) else 0.0
+    if len(idx) == 0:
+        return 0, worst
     with mpmath.workdps(34):
         zo = np.array([[mpmath.mpf(float(v)) for v in zs[i]] for i in idx], dtype=object)
         ref = Integrand(og)(zo, dtype=object)
         for j, i in enumerate(idx):
-            r = abs(mpmath.mpf(float(gpu[i])) - ref[j]) / abs(ref[j])
-            assert r < tol, (i, float(r), gpu[i], float(ref[j]))
+            r = float(abs(mpmath.mpf(float(gpu[i])) - ref[j]) / abs(ref[j]))
+            assert r < tol, (int(i), r, gpu[i], float(ref[j]))
+            worst = max(worst, r)
+    print(f"{og.pairs} e={og.e}: {len(rel)} points at {tol:g}, {len(idx)} settled by mpmath, "
+          f"largest verified error {worst:.2e}")
+    return len(idx), worst
 
 
 @pytest.mark.parametrize("n,gi", GRAPHS)
@@ -168,3 +178,23 @@ def test_empty_range_and_bad_arguments(ctx):
         ctx.load(q.Graph(2, ((0, 1), (2, 3)), 2))
     with pytest.raises(q.QedError):
         ctx.load(q.enumerate_graphs(1)[0], deg=np.zeros(8))
+
+
+def test_queue_overflow_rescan_matches_chunked_runs():
+    """More flagged points than the context's queue holds (2^22): the
+    double-double kernel re-scans the chunk and replaces the first pass.
+    The same samples in chunks that never overflow give the same estimate;
+    the flag decisions are taken by different kernels there, so the flagged
+    counts may differ by points at the threshold itself."""
+    c = q.Context(0, threshold=1e-13)
+    d = c.load(q.enumerate_graphs(2)[4])
+    n = 6_000_011
+    full = d.integrate(n, seed=17, begin=3)
+    assert full.n_flagged > (1 << 22)
+    parts = [d.integrate(2_000_000, seed=17, begin=3), d.integrate(2_000_000, seed=17, begin=2_000_003),
+             d.integrate(2_000_011, seed=17, begin=4_000_003)]
+    m = q.merge_results(q.merge_results(parts[0], parts[1]), parts[2])
+    assert m.n == full.n
+    assert abs(m.n_flagged - full.n_flagged) <= 1e-5 * n
+    assert m.value == pytest.approx(full.value, rel=1e-10)
+    assert m.variance == pytest.approx(full.variance, rel=1e-9)

@@ -84,7 +84,7 @@ def test_one_loop_gradient_matches_quadrature_derivative():
     beta = [0.1, 0.0, -0.2]
     f = Integrand(g)
     # score-function estimate over batches, for its error bar
-    est = [m2_grad(f, g, 0, 1, b * 20000, 20000, alpha, beta) for b in range(8)]
+    est = [m2_grad(f, g, 0, 1, b * 20000, 20000, alpha, beta, dtype=np.float64) for b in range(8)]
     m2 = np.mean([e[0] for e in est])
     ga = np.mean([e[1] for e in est], axis=0)
     ga_se = np.std([e[1] for e in est], axis=0, ddof=1) / math.sqrt(len(est))
