@@ -11,6 +11,12 @@ gradient is -E_p[w^2 d log p / d theta] (w = f/p).  This module computes it
 on given points, with d log Z / d theta by complex-step differentiation of
 the F recursion (Im log Z(theta + i h e_m) / h), an independent route from
 the reverse pass the CUDA library uses.
+
+Weights: w = f/p with f in long double at every point (the estimator's rule
+is to use each point's accurate value, re-evaluated at higher precision
+where the FP64 value loses digits to the cancellation between forest terms;
+the long-double value is that accurate value at every point of the graphs
+tested).  A non-finite w counts as 0.
 """
 from __future__ import annotations
 
@@ -125,14 +131,15 @@ def sample_theta(u, deg0, alpha, beta, N, d_min=0.05):
     return xs, lps, orders, deg, act, Z
 
 
-def m2_grad(integrand, g, stream_id, seed, begin, n, alpha, beta, d_min=0.05, deg0=None):
+def m2_grad(integrand, g, stream_id, seed, begin, n, alpha, beta, d_min=0.05, deg0=None,
+            dtype=np.longdouble):
     """(M2 estimate, dM2/dalpha, dM2/dbeta) on samples [begin, begin+n)."""
     from .graphs import deg_table
     N = g.n_lines
     deg0 = deg0 if deg0 is not None else deg_table(g)
     u = uniforms(np.arange(begin, begin + n, dtype=np.uint64), stream_id, seed, 2 * (N - 1))
     x, lp, order, deg, act, Z = sample_theta(u, deg0, alpha, beta, N, d_min)
-    w = integrand(x) * np.exp(-lp)
+    w = np.asarray(integrand(x, dtype=dtype), dtype=np.float64) * np.exp(-lp)
     w = np.where(np.isfinite(w), w, 0.0)
     w2 = w * w
     ga_s = np.zeros(N)
