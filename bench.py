@@ -225,8 +225,10 @@ def compare_plain(diags, graphs, ctx, S, seed, t_step, sigma_step, q):
             "total": sum(w * r.value for w, r in zip(mw, res)), "time_to_sigma": tts_plain,
             "kernel_seconds": sum(r.kernel_seconds for r in res),
             "speedup_time_to_sigma_batched_tuned_vs_plain": tts_plain / tts_batch,
-            "note": "the plain densities give heavy-tailed weights on the self-energy graphs, so "
-                    "this sigma is itself an underestimate"}
+            "note": ("a sigma is a reliable error bar where sigma sqrt(N) stays constant over a decade "
+                     "of samples: at two loops on both paths; at three loops on the calibrated, tuned "
+                     "path, not on the plain Deg-rule path (its weights are heavy-tailed); at four loops "
+                     "on neither")}
 
 
 def run_reference(args):
@@ -313,10 +315,13 @@ def run_native(args):
     torch.cuda.set_device(local)
     import paper_1905_08007_b300 as q
     from paper_1905_08007_b300.tune import tune
-    ctx = q.Context(local)
+    ctx = q.Context(local, threshold=args.threshold)
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream)
     graphs, mw = graph_set(q, args.order)
+    if args.graph_stride > 1:
+        # a smaller case of the same workload (every k-th graph), for profiling
+        graphs, mw = graphs[::args.graph_stride], mw[::args.graph_stride]
     S = int(args.samples if args.samples else DEFAULT_SAMPLES[args.order])
     total = S * len(graphs)
     fp64_peak = q.fp64_peak(local, 50.0)
@@ -336,6 +341,16 @@ def run_native(args):
             d.calibrate_deg(n_base=8, seed=args.seed + 5)
         if ts:
             tune(d, steps=ts, n=tn, lr=0.08, seed=args.seed + 7)
+    autotuned = None
+    if args.autotune and args.order >= 4:
+        from paper_1905_08007_b300.autotune import tune_batch_chunk, tune_vm
+        small = max(1 << 19, 4 * len(diags) * CHUNK[args.order])
+        best_vm, tab_vm = tune_vm(ctx, diags, samples=small, chunk=CHUNK[args.order])
+        best_ch, tab_ch = tune_batch_chunk(ctx, diags, samples=small,
+                                           chunks=(1 << 10, 1 << 11, 1 << 12))
+        if args.chunk is None:
+            args.chunk = best_ch["chunk"]
+        autotuned = {"vm": best_vm, "chunk": best_ch, "vm_table": tab_vm, "chunk_table": tab_ch}
     setup_s = time.perf_counter() - t0
     flops = [d.flops_per_sample() for d in diags]
     ddflops = []
@@ -391,13 +406,14 @@ def run_native(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         tmax, wmax = float(tt[0]), float(tt[1])
         gathered = [None] * ws
-        dist.all_gather_object(gathered, [(r.sum_w, r.sum_w2, r.n, r.n_flagged, r.n_unstable) for r in acc])
+        dist.all_gather_object(gathered, [(r.sum_w, r.sum_w2, r.n, r.n_flagged, r.n_unstable, r.unstable_abs_w)
+                                          for r in acc])
         results = []
         for i in range(len(diags)):
             m = None
             for rk in range(ws):
-                sw, sw2, n, nf, nu = gathered[rk][i]
-                r = q.Result(0.0, 0.0, tuple(sw), tuple(sw2), n, nf, nu, 0.0)
+                sw, sw2, n, nf, nu, uw = gathered[rk][i]
+                r = q.Result(0.0, 0.0, tuple(sw), tuple(sw2), n, nf, nu, 0.0, unstable_abs_w=uw)
                 m = r if m is None else q.merge_results(m, r)
             results.append(m)
     if rank != 0:
@@ -429,20 +445,27 @@ def run_native(args):
                                + {4: " (one per mirror pair, bytecode integrands)",
                                   5: " (the 64-graph workload, bytecode integrands)"}.get(args.order, "") + ", "
                                f"{total:.0e} Philox samples per step shared by running variance, "
-                               + {3: "gradient-tuned Deg-rule densities", 4: "gradient-tuned Deg-rule densities",
-                                  5: "Deg-rule densities"}.get(
-                                   args.order, "Deg-calibrated + gradient-tuned densities")
-                               + ", forest-subtracted FP64 integrand, double-double re-evaluation, "
+                               + ("Deg-rule densities" if args.order == 5 else
+                                  ("Deg-calibrated + gradient-tuned densities" if args.calibrate
+                                   else "gradient-tuned Deg-rule densities"))
+                               + f", forest-subtracted FP64 integrand, double-double re-evaluation above "
+                               f"{args.threshold:g}, "
                                "persistent batched kernel (4 CUDA-graph rounds per step)",
                    "loops": args.order, "graphs": len(graphs), "samples_per_step": total, "seed": args.seed, "l2_flush": True,
-                   "launch": {"threads": 256, "items_per_round": n_items, "chunk": chunk},
-                   "setup_seconds_calibrate_and_tune": setup_s},
+                   "flag_threshold": args.threshold, "deg": "calibrated" if args.calibrate else "rule",
+                   "launch": {"items_per_round": n_items, "chunk": chunk,
+                              **({"vm_threads": ctx.vm_shape[0], "vm_points": ctx.vm_shape[1]} if args.order >= 4
+                                 else {"threads": 256})},
+                   "setup_seconds_calibrate_and_tune": setup_s, "autotune": autotuned},
         "set_total": {"loops": args.order, "value": tot, "sigma": sigma,
                            "closed_form": CLOSED_FORM.get(args.order),
                            "pull": ((tot - CLOSED_FORM[args.order]) / sigma
                                     if sigma > 0 and args.order in CLOSED_FORM else None),
                            "flagged_fraction": flagged / total_samples,
                            "unstable": sum(r.n_unstable for r in results),
+                           # w := 0 at the unstable points; this is the most
+                           # that can have shifted the set total
+                           "unstable_abs_w_bound": sum(w * r.unstable_abs_w / r.n for w, r in zip(mw, results) if r.n),
                            "samples_per_graph": [r.n for r in results]},
         "time_to_sigma": {"target_sigma": SIGMA_TARGETS[args.order],
                           "seconds": tmax * (sigma / SIGMA_TARGETS[args.order]) ** 2,
@@ -465,7 +488,7 @@ def run_native(args):
                 "d2h_bytes_per_step": rounds * n_items * 96},
         "clocks": clk,
     }
-    if ws == 1 and args.compare and args.order in (2, 4):
+    if ws == 1 and args.compare and args.order in (2, 3, 4):
         line["plain_per_graph"] = compare_plain(diags, graphs, ctx, S, args.seed, tmax / args.steps, sigma, q)
     if ws == 1 and args.order != 2 and args.order <= 4:
         line["two_loop_total"] = two_loop_pull(q, ctx, args.seed)
@@ -487,14 +510,28 @@ def main(argv=None):
     ap.add_argument("--order", type=int, default=4, choices=[1, 2, 3, 4, 5], help="loop order of the graph set")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=None, help="samples per work item of the batched kernel")
+    ap.add_argument("--threshold", type=float, default=1e-6,
+                    help="relative rounding-error threshold above which a point is re-evaluated in "
+                         "double-double: at four loops every accepted point was measured within 0.55 x the "
+                         "threshold of its double-double value (2.4e-7 at 1e-6), far below any run's "
+                         "statistical error")
+    ap.add_argument("--graph-stride", type=int, default=1,
+                    help="every k-th graph of the set only (a small case for ncu captures)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default interpreter launch shape and work-item size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--calibrate", dest="calibrate", action="store_true", default=None,
+                    help="cap Deg by the integrand's measured exponents (default up to three loops)")
     ap.add_argument("--no-calibrate", dest="calibrate", action="store_false",
-                    help="Deg rule without the calibration on the integrand")
+                    help="the Deg rule without the calibration (default from four loops on: there "
+                         "the calibrated densities were measured to have heavier tails than the rule)")
     ap.add_argument("--no-compare", dest="compare", action="store_false",
                     help="skip the plain vs batched-tuned time-to-sigma comparison")
     a = ap.parse_args(argv)
     if a.warmup < 3:
         a.warmup = 3
+    if a.calibrate is None:
+        a.calibrate = a.order <= 3
     if a.impl == "reference":
         return run_reference(a)
     return run_native(a)

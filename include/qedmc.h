@@ -81,11 +81,16 @@ typedef struct {
   double sum_w2[2];               /* sum of w^2 as a double-double */
   uint64_t n;                     /* samples */
   uint64_t n_flagged;             /* points re-evaluated in double-double */
-  uint64_t n_unstable;            /* points unstable in double-double: w := 0 */
+  uint64_t n_unstable;            /* points unstable in double-double: w := 0
+                                     (see unstable_abs_w) */
   double seconds;                 /* device time of the call (all kernels) */
   double kernel_seconds;          /* device time of the FP64 integration kernel */
   uint32_t launches;              /* kernels launched by the call */
   double dd_seconds;              /* device time of the double-double kernels */
+  double unstable_abs_w;          /* sum of |w| over the unstable points (their
+                                     double-double value where finite): what
+                                     setting them to 0 can have removed from
+                                     sum_w, for context */
 } qed_result;
 
 /* ---- context ------------------------------------------------------------ */
@@ -260,7 +265,7 @@ int qed_fp64_peak(int device, double ms, double *flops_per_s);
  * further cudaMalloc, or a latency-critical loop where an allocation, which
  * can synchronise the device, is not acceptable.  The call allocates nothing
  * on the device or the host: its scratch is one file-scope device array of
- * 720,968 bytes (about 704 KiB) per GPU.  The GPU takes that memory when the
+ * 753,736 bytes (about 736 KiB) per GPU.  The GPU takes that memory when the
  * library's device code is loaded on it: under CUDA's default lazy module
  * loading that is the first use of the library's device code on that
  * device (this call's address lookup, or any other call that launches a

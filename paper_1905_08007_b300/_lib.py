@@ -45,7 +45,8 @@ class _Result(C.Structure):
     _fields_ = [("value", C.c_double), ("variance", C.c_double), ("sum_w", C.c_double * 2),
                 ("sum_w2", C.c_double * 2), ("n", C.c_uint64), ("n_flagged", C.c_uint64),
                 ("n_unstable", C.c_uint64), ("seconds", C.c_double),
-                ("kernel_seconds", C.c_double), ("launches", C.c_uint32), ("dd_seconds", C.c_double)]
+                ("kernel_seconds", C.c_double), ("launches", C.c_uint32), ("dd_seconds", C.c_double),
+                ("unstable_abs_w", C.c_double)]
 
 
 @dataclass(frozen=True)
@@ -86,6 +87,7 @@ class Result:
     kernel_seconds: float = 0.0
     launches: int = 0
     dd_seconds: float = 0.0
+    unstable_abs_w: float = 0.0
 
     @property
     def sigma(self):
@@ -98,12 +100,14 @@ class Result:
         r.sum_w2[0], r.sum_w2[1] = self.sum_w2
         r.n, r.n_flagged, r.n_unstable, r.seconds = self.n, self.n_flagged, self.n_unstable, self.seconds
         r.kernel_seconds, r.launches, r.dd_seconds = self.kernel_seconds, self.launches, self.dd_seconds
+        r.unstable_abs_w = self.unstable_abs_w
         return r
 
     @staticmethod
     def _from_c(r):
         return Result(r.value, r.variance, (r.sum_w[0], r.sum_w[1]), (r.sum_w2[0], r.sum_w2[1]),
-                      r.n, r.n_flagged, r.n_unstable, r.seconds, r.kernel_seconds, r.launches, r.dd_seconds)
+                      r.n, r.n_flagged, r.n_unstable, r.seconds, r.kernel_seconds, r.launches, r.dd_seconds,
+                      r.unstable_abs_w)
 
 
 _LIB = None
@@ -224,6 +228,7 @@ class Context:
         _check(L.qed_ctx_create(device, QED_CTX_PREFER_PROGRAMS if prefer_programs else 0, C.byref(self._h)))
         self.device = device
         self.n_programs = 0
+        self.vm_shape = (128, 1)
         if programs:
             import zlib
             for f in program_files():
@@ -245,6 +250,7 @@ class Context:
     def set_vm(self, threads: int = 128, points: int = 1):
         """qed_ctx_set_vm: block size and points per thread of the interpreter kernels."""
         _check(load_library().qed_ctx_set_vm(self._h, threads, points))
+        self.vm_shape = (threads, points)
 
     def set_launch(self, threads: int, blocks: int = 0):
         _check(load_library().qed_ctx_set_launch(self._h, threads, blocks))

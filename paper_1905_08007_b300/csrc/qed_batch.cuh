@@ -40,11 +40,11 @@ struct BatchParams {
   unsigned int *next_item;          // work counter, zeroed every round
   uint32_t key0, key1;
   double thresh;
-  double *part;                     // [n_items][4]  FP64 moments
+  double *part;                     // [n_items][QED_PART]  FP64 moments
   unsigned long long *cnt;          // [n_items][2]  flagged, (unused)
   uint32_t *lists;                  // [n_items][list_cap] flagged offsets
   uint32_t list_cap;
-  double *part_dd;                  // [n_items * dd_tiles][4]  double-double moments
+  double *part_dd;                  // [n_items * dd_tiles][QED_PART]  double-double moments
   unsigned long long *cnt_dd;       // [n_items * dd_tiles][2]  (unused), unstable
   uint32_t dd_tiles;                // double-double tiles per item (1: one block per item)
   unsigned int *next_tile;          // tile counter of the bytecode dd pass, zeroed every round
@@ -115,16 +115,25 @@ __device__ __forceinline__ void batch_item_dd(const BatchParams &B, unsigned int
   const bool overflow = nflag > B.list_cap;
   const uint64_t total = overflow ? uint64_t(I.count) : nflag;
   KSum sw, sw2;
-  unsigned long long nunst = 0;
+  unsigned long long nflg = 0, nunst = 0;
+  double uw = 0.0;
   for (uint64_t i = threadIdx.x; i < total; i += blockDim.x) {
     const uint32_t off = overflow ? uint32_t(i) : B.lists[size_t(it) * B.list_cap + i];
     double z[N];
     const double lp = draw_point<N>(I.begin + off, P, sF, sG, sInv, z);
-    if (overflow) {      // the list overflowed: find the flagged samples again
+    if (overflow) {
+      // the list overflowed: this pass evaluates the whole item again and
+      // replaces the FP64 pass's sums for it (the host uses this pass
+      // alone), so each point is accepted or flagged by one decision
       double ab;
       const double f0 = qed_gen_f<FID>::template eval<double>(z, ab);
       const double w0 = f0 * exp(-lp);
-      if (isfinite(w0) && rel_err_estimate(f0, ab, 1.1102230246251565e-16) <= P.thresh) continue;
+      if (isfinite(w0) && rel_err_estimate(f0, ab, 1.1102230246251565e-16) <= P.thresh) {
+        sw.add(w0);
+        sw2.add(w0 * w0);
+        continue;
+      }
+      ++nflg;
     }
     dd zd[N];
 #pragma unroll
@@ -132,11 +141,15 @@ __device__ __forceinline__ void batch_item_dd(const BatchParams &B, unsigned int
     double absum;
     const dd f = qed_gen_f<FID>::template eval<dd>(zd, absum);
     const double w = (f.hi + f.lo) * exp(-lp);
-    if (!isfinite(w) || !(rel_err_estimate(f.hi, absum, 1.2325951644078309e-32) <= P.thresh)) { ++nunst; continue; }
+    if (!isfinite(w) || !(rel_err_estimate(f.hi, absum, 1.2325951644078309e-32) <= P.thresh)) {
+      ++nunst;
+      if (isfinite(w)) uw += fabs(w);
+      continue;
+    }
     sw.add(w);
     sw2.add(w * w);
   }
-  block_reduce_store(sw, sw2, 0ull, nunst, B.part_dd, B.cnt_dd, it);
+  block_reduce_store(sw, sw2, nflg, nunst, B.part_dd, B.cnt_dd, it, uw);
 }
 
 // The generated batch translation unit defines QED_BATCH_TU, includes every
@@ -167,8 +180,8 @@ __global__ void __launch_bounds__(256) k_batch_dd(BatchParams B) {
     const BatchItem I = B.items[it];
     if (B.cnt[2 * size_t(it)] == 0) {
       if (threadIdx.x == 0) {
-        double *p = B.part_dd + 4 * size_t(it);
-        p[0] = p[1] = p[2] = p[3] = 0.0;
+        double *p = B.part_dd + QED_PART * size_t(it);
+        p[0] = p[1] = p[2] = p[3] = p[4] = 0.0;
         B.cnt_dd[2 * size_t(it)] = 0;
         B.cnt_dd[2 * size_t(it) + 1] = 0;
       }

@@ -44,7 +44,7 @@ struct KParams {
   uint32_t key0, key1, stream;
   double thresh;          // relative rounding-error threshold
   // outputs
-  double *partials;       // [gridDim.x][4]: sum w (hi, lo), sum w^2 (hi, lo)
+  double *partials;       // [gridDim.x][QED_PART]: sum w (hi, lo), sum w^2 (hi, lo), unstable sum |w|
   unsigned long long *counts;   // [gridDim.x][2]: flagged, unstable
   unsigned long long *queue;    // flagged sample offsets
   unsigned int *queue_len;
@@ -153,11 +153,16 @@ struct KSum {
   }
 };
 
+// Doubles per partial slot: sum w (hi, lo), sum w^2 (hi, lo), and the sum
+// of |w| over the points that failed the threshold in double-double too.
+#define QED_PART 5
+
 // Reduce (hi, lo) pairs of a block into partials[slot] (slot = blockIdx.x
 // for the per-graph kernels, the work-item index for the batched kernels).
+// uw: this thread's sum of |w| over its unstable points (0 in FP64 passes).
 __device__ __forceinline__ void block_reduce_store(KSum a, KSum b, unsigned long long nf, unsigned long long nu,
                                                    double *partials, unsigned long long *counts,
-                                                   unsigned int slot) {
+                                                   unsigned int slot, double uw = 0.0) {
   dd x = dd_from_sum(a.s, a.c), y = dd_from_sum(b.s, b.c);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -167,23 +172,29 @@ __device__ __forceinline__ void block_reduce_store(KSum a, KSum b, unsigned long
     y = y + yo;
     nf += __shfl_down_sync(0xffffffffu, nf, o);
     nu += __shfl_down_sync(0xffffffffu, nu, o);
+    uw += __shfl_down_sync(0xffffffffu, uw, o);
   }
-  __shared__ double red[32][4];
+  __shared__ double red[32][QED_PART];
   __shared__ unsigned long long redc[32][2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) { red[warp][0] = x.hi; red[warp][1] = x.lo; red[warp][2] = y.hi; red[warp][3] = y.lo; redc[warp][0] = nf; redc[warp][1] = nu; }
+  if (lane == 0) {
+    red[warp][0] = x.hi; red[warp][1] = x.lo; red[warp][2] = y.hi; red[warp][3] = y.lo; red[warp][4] = uw;
+    redc[warp][0] = nf; redc[warp][1] = nu;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     dd X{0.0, 0.0}, Y{0.0, 0.0};
+    double Uw = 0.0;
     unsigned long long F = 0, Un = 0;
     for (int w = 0; w < int(blockDim.x >> 5); ++w) {
       X = X + dd{red[w][0], red[w][1]};
       Y = Y + dd{red[w][2], red[w][3]};
+      Uw += red[w][4];
       F += redc[w][0];
       Un += redc[w][1];
     }
-    double *p = partials + 4 * size_t(slot);
-    p[0] = X.hi; p[1] = X.lo; p[2] = Y.hi; p[3] = Y.lo;
+    double *p = partials + QED_PART * size_t(slot);
+    p[0] = X.hi; p[1] = X.lo; p[2] = Y.hi; p[3] = Y.lo; p[4] = Uw;
     counts[2 * size_t(slot)] = F;
     counts[2 * size_t(slot) + 1] = Un;
   }
@@ -233,6 +244,7 @@ __global__ void __launch_bounds__(256) k_redo_dd(KParams P, int mode, unsigned i
   load_tables<N>(P, sF, sG, sInv);
   KSum sw, sw2;
   unsigned long long nflag = 0, nunst = 0;
+  double uw = 0.0;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   const uint64_t total = mode == 0 ? uint64_t(qn) : P.n;
   for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += stride) {
@@ -259,12 +271,13 @@ __global__ void __launch_bounds__(256) k_redo_dd(KParams P, int mode, unsigned i
     const double w = (f.hi + f.lo) * exp(-lp);
     if (!isfinite(w) || !(rel_err_estimate(f.hi, absum, 1.2325951644078309e-32) <= P.thresh)) {
       ++nunst;
+      if (isfinite(w)) uw += fabs(w);
       continue;
     }
     sw.add(w);
     sw2.add(w * w);
   }
-  block_reduce_store(sw, sw2, nflag, nunst, P.partials, P.counts, blockIdx.x);
+  block_reduce_store(sw, sw2, nflag, nunst, P.partials, P.counts, blockIdx.x, uw);
 }
 
 template <int FID, int N>

@@ -351,6 +351,7 @@ __global__ void __launch_bounds__(256) k_redo_dd_vm(KParams K, VmCode C, unsigne
   fr.setup(C, vsm);
   KSum sw, sw2;
   unsigned long long nunst = 0;
+  double uw = 0.0;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < qn; i += stride) {
     double z[N];
@@ -363,12 +364,13 @@ __global__ void __launch_bounds__(256) k_redo_dd_vm(KParams K, VmCode C, unsigne
     const double w = (f[0].hi + f[0].lo) * exp(-lp);
     if (!isfinite(w) || !(rel_err_estimate(f[0].hi, ab[0], 1.2325951644078309e-32) <= K.thresh)) {
       ++nunst;
+      if (isfinite(w)) uw += fabs(w);
       continue;
     }
     sw.add(w);
     sw2.add(w * w);
   }
-  block_reduce_store(sw, sw2, 0ull, nunst, K.partials, K.counts, blockIdx.x);
+  block_reduce_store(sw, sw2, 0ull, nunst, K.partials, K.counts, blockIdx.x, uw);
 }
 
 template <int N, int P>
@@ -591,8 +593,8 @@ __global__ void __launch_bounds__(256) k_batch_vm_dd(BatchParams B) {
     const uint64_t start = uint64_t(k) * blockDim.x;
     if (start >= total) {
       if (threadIdx.x == 0) {
-        double *p = B.part_dd + 4 * size_t(t);
-        p[0] = p[1] = p[2] = p[3] = 0.0;
+        double *p = B.part_dd + QED_PART * size_t(t);
+        p[0] = p[1] = p[2] = p[3] = p[4] = 0.0;
         B.cnt_dd[2 * size_t(t)] = 0;
         B.cnt_dd[2 * size_t(t) + 1] = 0;
       }
@@ -606,6 +608,7 @@ __global__ void __launch_bounds__(256) k_batch_vm_dd(BatchParams B) {
     fr.setup(C, vsm);
     KSum sw, sw2;
     unsigned long long nunst = 0;
+    double uw = 0.0;
     const uint64_t i = start + threadIdx.x;
     if (i < total) {
       const uint32_t off = B.lists[size_t(it) * B.list_cap + i];
@@ -617,10 +620,15 @@ __global__ void __launch_bounds__(256) k_batch_vm_dd(BatchParams B) {
       for (int L = 0; L < N; ++L) zd[0][L] = dd{z[L], 0.0};
       fr.template eval<N>(C, zd, f, ab);
       const double w = (f[0].hi + f[0].lo) * exp(-lp);
-      if (!isfinite(w) || !(rel_err_estimate(f[0].hi, ab[0], 1.2325951644078309e-32) <= K.thresh)) ++nunst;
-      else { sw.add(w); sw2.add(w * w); }
+      if (!isfinite(w) || !(rel_err_estimate(f[0].hi, ab[0], 1.2325951644078309e-32) <= K.thresh)) {
+        ++nunst;
+        if (isfinite(w)) uw += fabs(w);
+      } else {
+        sw.add(w);
+        sw2.add(w * w);
+      }
     }
-    block_reduce_store(sw, sw2, 0ull, nunst, B.part_dd, B.cnt_dd, t);
+    block_reduce_store(sw, sw2, 0ull, nunst, B.part_dd, B.cnt_dd, t, uw);
   }
 }
 

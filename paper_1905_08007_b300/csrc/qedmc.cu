@@ -163,10 +163,10 @@ static int ensure_scratch(qed_ctx *c, int blocks) {
   if (c->partials) cudaFree(c->partials);
   if (c->counts) cudaFree(c->counts);
   c->partials = nullptr; c->counts = nullptr;
-  CUDA_TRY(cudaMalloc(&c->partials, size_t(blocks) * 4 * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&c->partials, size_t(blocks) * QED_PART * sizeof(double)));
   CUDA_TRY(cudaMalloc(&c->counts, size_t(blocks) * 2 * sizeof(unsigned long long)));
   c->partial_cap = blocks;
-  c->h_partials.resize(size_t(blocks) * 4);
+  c->h_partials.resize(size_t(blocks) * QED_PART);
   c->h_counts.resize(size_t(blocks) * 2);
   return QED_OK;
 }
@@ -620,12 +620,14 @@ static void dd_acc(double &hi, double &lo, double a_hi, double a_lo) {
 }
 
 static int fold(qed_ctx *c, int blocks, qed_result *r, bool add_flagged_as_count) {
-  CUDA_TRY(cudaMemcpyAsync(c->h_partials.data(), c->partials, size_t(blocks) * 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaMemcpyAsync(c->h_partials.data(), c->partials, size_t(blocks) * QED_PART * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaMemcpyAsync(c->h_counts.data(), c->counts, size_t(blocks) * 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   for (int b = 0; b < blocks; ++b) {
-    dd_acc(r->sum_w[0], r->sum_w[1], c->h_partials[4 * b], c->h_partials[4 * b + 1]);
-    dd_acc(r->sum_w2[0], r->sum_w2[1], c->h_partials[4 * b + 2], c->h_partials[4 * b + 3]);
+    const double *pb = c->h_partials.data() + QED_PART * size_t(b);
+    dd_acc(r->sum_w[0], r->sum_w[1], pb[0], pb[1]);
+    dd_acc(r->sum_w2[0], r->sum_w2[1], pb[2], pb[3]);
+    r->unstable_abs_w += pb[4];
     if (add_flagged_as_count) r->n_flagged += c->h_counts[2 * b];
     r->n_unstable += c->h_counts[2 * b + 1];
   }
@@ -774,6 +776,7 @@ extern "C" int qed_result_merge(const qed_result *a, const qed_result *b, qed_re
   r.n_flagged = a->n_flagged + b->n_flagged;
   r.n_unstable = a->n_unstable + b->n_unstable;
   r.seconds = a->seconds + b->seconds;
+  r.unstable_abs_w = a->unstable_abs_w + b->unstable_abs_w;
   r.dd_seconds = a->dd_seconds + b->dd_seconds;
   r.kernel_seconds = a->kernel_seconds + b->kernel_seconds;
   r.launches = a->launches + b->launches;
@@ -927,8 +930,8 @@ struct BatchPlan {
     CUDA_TRY(cudaEventRecordWithFlags(c->evk1, s, evflags));
     CUDA_TRY(cudaLaunchKernel(kern2, dim3(grid2), dim3(thr2), args, smem2, s));
     CUDA_TRY(cudaEventRecordWithFlags(c->evk2, s, evflags));
-    CUDA_TRY(cudaMemcpyAsync(o_part, dev[3], sizeof(double) * 4 * n_items, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(o_pdd, dev[5], sizeof(double) * 4 * n_dd, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(o_part, dev[3], sizeof(double) * QED_PART * n_items, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(o_pdd, dev[5], sizeof(double) * QED_PART * n_dd, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(o_cnt, dev[4], sizeof(unsigned long long) * 2 * n_items, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(o_cdd, dev[6], sizeof(unsigned long long) * 2 * n_dd, cudaMemcpyDeviceToHost, s));
     return QED_OK;
@@ -939,18 +942,18 @@ struct BatchPlan {
     CUDA_TRY(cudaMalloc(&dev[0], sizeof(BatchDiag) * k));
     CUDA_TRY(cudaMalloc(&dev[1], sizeof(BatchItem) * n_items));
     CUDA_TRY(cudaMalloc(&dev[2], 2 * sizeof(unsigned int)));
-    CUDA_TRY(cudaMalloc(&dev[3], sizeof(double) * 4 * n_items));
+    CUDA_TRY(cudaMalloc(&dev[3], sizeof(double) * QED_PART * n_items));
     CUDA_TRY(cudaMalloc(&dev[4], sizeof(unsigned long long) * 2 * n_items));
-    CUDA_TRY(cudaMalloc(&dev[5], sizeof(double) * 4 * n_dd));
+    CUDA_TRY(cudaMalloc(&dev[5], sizeof(double) * QED_PART * n_dd));
     CUDA_TRY(cudaMalloc(&dev[6], sizeof(unsigned long long) * 2 * n_dd));
     CUDA_TRY(cudaMalloc(&dev[7], sizeof(uint32_t) * size_t(list_cap) * n_items));
-    const size_t out_bytes = n_items * (4 * sizeof(double) + 2 * sizeof(unsigned long long)) +
-                             n_dd * (4 * sizeof(double) + 2 * sizeof(unsigned long long));
+    const size_t out_bytes = n_items * (QED_PART * sizeof(double) + 2 * sizeof(unsigned long long)) +
+                             n_dd * (QED_PART * sizeof(double) + 2 * sizeof(unsigned long long));
     CUDA_TRY(cudaMallocHost(&h_items, sizeof(BatchItem) * n_items));
     CUDA_TRY(cudaMallocHost(&h_out, out_bytes));
     o_part = (double *)h_out;
-    o_pdd = o_part + 4 * size_t(n_items);
-    o_cnt = (unsigned long long *)(o_pdd + 4 * n_dd);
+    o_pdd = o_part + QED_PART * size_t(n_items);
+    o_cnt = (unsigned long long *)(o_pdd + QED_PART * n_dd);
     o_cdd = o_cnt + 2 * size_t(n_items);
     B.diags = (const BatchDiag *)dev[0]; B.items = (const BatchItem *)dev[1]; B.n_items = n_items;
     B.next_item = (unsigned int *)dev[2]; B.key0 = uint32_t(seed); B.key1 = uint32_t(seed >> 32);
@@ -1127,16 +1130,26 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
     }
     for (unsigned int i = 0; i < n_items; ++i) {
       qed_result &q = R[hi[i].diag];
-      dd_acc(q.sum_w[0], q.sum_w[1], o_part[4 * i], o_part[4 * i + 1]);
-      dd_acc(q.sum_w2[0], q.sum_w2[1], o_part[4 * i + 2], o_part[4 * i + 3]);
+      // an item whose flagged list overflowed (compiled batches: list_cap is
+      // chunk / list_div) was evaluated again in full by the double-double
+      // pass, which alone decides its points: its FP64 sums are not used
+      const bool overflow = !vmb && o_cnt[2 * size_t(i)] > list_cap;
+      if (!overflow) {
+        const double *p = o_part + QED_PART * size_t(i);
+        dd_acc(q.sum_w[0], q.sum_w[1], p[0], p[1]);
+        dd_acc(q.sum_w2[0], q.sum_w2[1], p[2], p[3]);
+        q.n_flagged += o_cnt[2 * size_t(i)];
+      }
       for (uint32_t kt = 0; kt < dd_tiles; ++kt) {
         const size_t t = size_t(i) * dd_tiles + kt;
-        dd_acc(q.sum_w[0], q.sum_w[1], o_pdd[4 * t], o_pdd[4 * t + 1]);
-        dd_acc(q.sum_w2[0], q.sum_w2[1], o_pdd[4 * t + 2], o_pdd[4 * t + 3]);
+        const double *p = o_pdd + QED_PART * t;
+        dd_acc(q.sum_w[0], q.sum_w[1], p[0], p[1]);
+        dd_acc(q.sum_w2[0], q.sum_w2[1], p[2], p[3]);
+        q.unstable_abs_w += p[4];
         q.n_unstable += o_cdd[2 * t + 1];
+        if (overflow) q.n_flagged += o_cdd[2 * t];
       }
       q.n += hi[i].count;
-      q.n_flagged += o_cnt[2 * i];
     }
     // Neyman weights: sigma_g / sqrt(cost_g), cost = FP64 ops per sample with
     // flagged samples counted at the double-double factor
@@ -1359,34 +1372,36 @@ extern "C" int qed_diagram_get_deg(const qed_diag *d, double *deg_out) {
 #define QED_NOALLOC_MAX_BLOCKS 2048
 #define QED_NOALLOC_QUEUE 65536
 struct NoAllocScratch {
-  double part[2][QED_NOALLOC_MAX_BLOCKS][4];              // FP64 pass, double-double pass
+  double part[2][QED_NOALLOC_MAX_BLOCKS][QED_PART];       // FP64 pass, double-double pass
   unsigned long long cnt[2][QED_NOALLOC_MAX_BLOCKS][2];
   unsigned long long queue[QED_NOALLOC_QUEUE];
   double result[8];                                       // folded sums (see k_noalloc_fold)
   unsigned int queue_len;
 };
-static_assert(sizeof(NoAllocScratch) == 720968, "the header states this size");
-// Every GPU that loads the library holds this array (720,968 bytes, about
-// 704 KiB) from the moment the library's module is loaded on it until the
+static_assert(sizeof(NoAllocScratch) == 753736, "the header states this size");
+// Every GPU that loads the library holds this array (753,736 bytes, about
+// 736 KiB) from the moment the library's module is loaded on it until the
 // process exits.
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
 // Folds the per-block partials of passes [p_begin, p_end) (0 = FP64, 1 =
 // double-double) in block order, in double-double: result = {sum w (hi, lo),
-// sum w^2 (hi, lo), flagged, unstable}.
+// sum w^2 (hi, lo), flagged, unstable, sum |w| over the unstable points}.
 __global__ void k_noalloc_fold(NoAllocScratch *s, int blocks, int p_begin, int p_end) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   dd x{0.0, 0.0}, y{0.0, 0.0};
+  double uw = 0.0;
   unsigned long long nf = 0, nu = 0;
   for (int p = p_begin; p < p_end; ++p)
     for (int b = 0; b < blocks; ++b) {
       x = x + dd{s->part[p][b][0], s->part[p][b][1]};
       y = y + dd{s->part[p][b][2], s->part[p][b][3]};
+      uw += s->part[p][b][4];
       nf += s->cnt[p][b][0];
       nu += s->cnt[p][b][1];
     }
   s->result[0] = x.hi; s->result[1] = x.lo; s->result[2] = y.hi; s->result[3] = y.lo;
-  s->result[4] = double(nf); s->result[5] = double(nu);
+  s->result[4] = double(nf); s->result[5] = double(nu); s->result[6] = uw;
 }
 
 static std::mutex g_noalloc_mu;
@@ -1464,7 +1479,7 @@ extern "C" int qed_integrate_range_noalloc(qed_diag *d, uint64_t begin, uint64_t
     }
     void *args3[] = {&S, (void *)&blocks, &p_begin, &p_end};
     if ((rc = launch((const void *)k_noalloc_fold, 1, 32, 0, c->stream, args3))) return rc;
-    double res[6];
+    double res[7];
     CUDA_TRY(cudaMemcpyAsync(res, S->result, sizeof res, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (dd_timed) {
@@ -1476,6 +1491,7 @@ extern "C" int qed_integrate_range_noalloc(qed_diag *d, uint64_t begin, uint64_t
     dd_acc(r.sum_w2[0], r.sum_w2[1], res[2], res[3]);
     r.n_flagged += (unsigned long long)res[4];
     r.n_unstable += (unsigned long long)res[5];
+    r.unstable_abs_w += res[6];
   }
   CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
   CUDA_TRY(cudaEventSynchronize(c->ev1));

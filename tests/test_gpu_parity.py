@@ -186,7 +186,7 @@ def test_queue_overflow_rescan_matches_chunked_runs():
     The same samples in chunks that never overflow give the same estimate;
     the flag decisions are taken by different kernels there, so the flagged
     counts may differ by points at the threshold itself."""
-    c = q.Context(0, threshold=1e-13)
+    c = q.Context(0, threshold=1e-15)
     d = c.load(q.enumerate_graphs(2)[4])
     n = 6_000_011
     full = d.integrate(n, seed=17, begin=3)

@@ -163,7 +163,9 @@ def test_four_loop_programs_match_stored_oracle():
     for r in rows:
         byg.setdefault(int(r[0]), []).append(r)
     assert len(byg) >= 4
-    for gi, rs in byg.items():
+    # every eighth stored graph here (a numpy interpretation of a four-loop
+    # program takes seconds); the GPU test covers every stored graph
+    for gi, rs in sorted(byg.items())[::8]:
         z = np.array([[float(v) for v in r[3:15]] for r in rs])
         fo = np.array([np.longdouble(r[15]) for r in rs])
         fv, W = interpret(progs[_name(gs[gi])], z, np.longdouble)
