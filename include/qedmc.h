@@ -122,6 +122,40 @@ int qed_ctx_set_vm(qed_ctx *ctx, int threads_per_block, int points_per_thread);
  * 8 ulp x (sum of the absolute values of the integrand's monomials) / |f|; the
  * double-double result is accepted under the same rule with its own ulp. */
 int qed_ctx_set_threshold(qed_ctx *ctx, double rel_err);
+/* Generator of the sample points (Sec. 3 integrates with two generators of
+ * the CURAND library as an independent check: MRG32k3a in Calc 1,
+ * Philox4x32-10 in Calc 2).  QED_RNG_PHILOX (default): the Philox layout of
+ * the conventions above.  QED_RNG_MRG32K3A: L'Ecuyer's MRG32k3a started from
+ * the state with all six words 12345; sample s of a graph with stream id g
+ * under seed k takes its draws 0..2N-3 from positions
+ * k * 2^127 + g * 2^96 + s * 2^5 + d of that sequence (32 draws per sample,
+ * jumps by matrix powers), u = z / (m1 + 1) computed as z times the double
+ * nearest 1 / (m1 + 1) (32 random bits).  Applies to every later launch on
+ * the context; results depend on (generator, seed, stream id, sample range,
+ * launch shape) as above.  Other values: QED_EINVAL. */
+#define QED_RNG_PHILOX 0
+#define QED_RNG_MRG32K3A 1
+int qed_ctx_set_rng(qed_ctx *ctx, int rng);
+/* Which points the double-double pass re-evaluates (Sec. 3: the round-off
+ * of the numerical subtraction is removed with interval arithmetic of
+ * different precisions).
+ * QED_FLAG_ESTIMATE (default): the FP64 value with its rounding-error
+ * estimate (qed_ctx_set_threshold).
+ * QED_FLAG_INTERVAL: every point is evaluated in FP64 interval arithmetic
+ * (each operation rounds the lower end down and the upper end up, so the
+ * interval encloses the exact value of the program's arithmetic); the
+ * midpoint is accepted when both ends have one sign and
+ * hi - lo <= 2 threshold min(|lo|, |hi|), a rigorous bound of its relative
+ * error by the threshold; other points are re-evaluated in double-double
+ * (accepted there by the estimate).  Bytecode programs only: on this rule
+ * qed_integrate / qed_integrate_range of a graph with a compiled integrand,
+ * qed_integrate_batch and qed_integrate_range_noalloc give QED_EINVAL (load
+ * the graph on a QED_CTX_PREFER_PROGRAMS context to use its program);
+ * qed_pdf_grad and qed_dump_points keep the estimate.  Other values:
+ * QED_EINVAL. */
+#define QED_FLAG_ESTIMATE 0
+#define QED_FLAG_INTERVAL 1
+int qed_ctx_set_flag_rule(qed_ctx *ctx, int rule);
 const char *qed_last_error(void);
 
 /* ---- graphs ------------------------------------------------------------- */
@@ -175,6 +209,16 @@ int qed_dump_points(qed_diag *d, uint64_t begin, uint64_t n, uint64_t seed,
 /* Evaluate the integrand at caller-supplied DEVICE points z (n x N) in FP64
  * (prec = 0) or double-double (prec = 1, result rounded to double). */
 int qed_eval_points(qed_diag *d, const double *z_dev, uint64_t n, int prec, double *f_dev);
+
+/* FP64 interval arithmetic at caller-supplied DEVICE points z (n x N):
+ * lo_dev[i] <= (exact value of the program's arithmetic at z_i) <= hi_dev[i]
+ * (Sec. 3, interval arithmetic; see QED_FLAG_INTERVAL).  The program's
+ * constants are the FP64 roundings of the generated coefficients, so the
+ * exact integrand can differ from the enclosed value by that rounding (a
+ * few ulp of the sum of the absolute values of the monomials).  An interval
+ * that lost every digit comes back as [-inf, inf] or with NaN ends.
+ * Bytecode programs only (QED_EINVAL for a compiled integrand). */
+int qed_eval_interval(qed_diag *d, const double *z_dev, uint64_t n, double *lo_dev, double *hi_dev);
 
 /* ---- tunable density and the adjoint of the second moment --------------- */
 /* Set the density's parameters theta (Sec. 2 builds the density from Deg;

@@ -20,3 +20,4 @@ from ._lib import (  # noqa: F401
     merge_results,
     fp64_peak,
 )
+from .classes import class_table  # noqa: F401

@@ -159,6 +159,9 @@ def load_library():
         "qed_diagram_get_deg": (C.c_int, [C.c_void_p, P(C.c_double)]),
         "qed_programs_load": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, P(C.c_int)]),
         "qed_ctx_set_vm": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+        "qed_ctx_set_rng": (C.c_int, [C.c_void_p, C.c_int]),
+        "qed_ctx_set_flag_rule": (C.c_int, [C.c_void_p, C.c_int]),
+        "qed_eval_interval": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -205,6 +208,10 @@ def merge_results(a: Result, b: Result) -> Result:
 
 
 QED_CTX_PREFER_PROGRAMS = 1
+# generators of the sample points (qed_ctx_set_rng)
+RNGS = {"philox": 0, "mrg32k3a": 1}
+# which points the double-double pass re-evaluates (qed_ctx_set_flag_rule)
+FLAG_RULES = {"estimate": 0, "interval": 1}
 
 
 def program_files():
@@ -222,7 +229,7 @@ class Context:
 
     def __init__(self, device: int = 0, threads: int | None = None, blocks: int | None = None,
                  threshold: float | None = None, stream=None, programs: bool = True,
-                 prefer_programs: bool = False):
+                 prefer_programs: bool = False, rng: str = "philox", flag_rule: str = "estimate"):
         L = load_library()
         self._h = C.c_void_p()
         _check(L.qed_ctx_create(device, QED_CTX_PREFER_PROGRAMS if prefer_programs else 0, C.byref(self._h)))
@@ -239,6 +246,27 @@ class Context:
             _check(L.qed_ctx_set_threshold(self._h, threshold))
         if stream is not None:
             self.set_stream(stream)
+        self.rng = "philox"
+        if rng != "philox":
+            self.set_rng(rng)
+        self.flag_rule = "estimate"
+        if flag_rule != "estimate":
+            self.set_flag_rule(flag_rule)
+
+    def set_flag_rule(self, rule: str):
+        """qed_ctx_set_flag_rule: "estimate" (FP64 rounding-error estimate) or
+        "interval" (FP64 interval arithmetic, bytecode programs)."""
+        if rule not in FLAG_RULES:
+            raise QedError(-1, f"unknown flag rule {rule!r}")
+        _check(load_library().qed_ctx_set_flag_rule(self._h, FLAG_RULES[rule]))
+        self.flag_rule = rule
+
+    def set_rng(self, rng: str):
+        """qed_ctx_set_rng: "philox" (Philox4x32-10) or "mrg32k3a"."""
+        if rng not in RNGS:
+            raise QedError(-1, f"unknown generator {rng!r}")
+        _check(load_library().qed_ctx_set_rng(self._h, RNGS[rng]))
+        self.rng = rng
 
     def programs_load(self, data: bytes) -> int:
         """qed_programs_load: register the bytecode integrands of a program file."""
@@ -338,6 +366,18 @@ class Diagram:
         torch.cuda.synchronize(z.device)
         _check(load_library().qed_eval_points(self._h, z.data_ptr(), z.shape[0], prec, f.data_ptr()))
         return f
+
+    def eval_interval(self, z):
+        """qed_eval_interval: FP64 interval enclosure (lo, hi) at points z
+        (torch CUDA float64 [n, N]); bytecode programs only."""
+        import torch
+        z = z.contiguous()
+        assert z.dtype == torch.float64 and z.is_cuda and z.shape[1] == self.n_lines
+        lo = torch.empty(z.shape[0], dtype=torch.float64, device=z.device)
+        hi = torch.empty_like(lo)
+        torch.cuda.synchronize(z.device)
+        _check(load_library().qed_eval_interval(self._h, z.data_ptr(), z.shape[0], lo.data_ptr(), hi.data_ptr()))
+        return lo, hi
 
     def calibrate_deg(self, n_base: int = 8, seed: int = 0):
         """Cap Deg(s) by the measured growth of the integrand in each limit."""

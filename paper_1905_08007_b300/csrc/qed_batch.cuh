@@ -25,6 +25,8 @@ struct BatchDiag {
   const uint2 *vins;
   const double *vkon;
   int vnk, vnr;
+  uint32_t mrg[6];                  // MRG32k3a start state of this graph's stream
+  uint32_t pad2[2];
 };
 
 struct BatchItem {
@@ -48,6 +50,8 @@ struct BatchParams {
   unsigned long long *cnt_dd;       // [n_items * dd_tiles][2]  (unused), unstable
   uint32_t dd_tiles;                // double-double tiles per item (1: one block per item)
   unsigned int *next_tile;          // tile counter of the bytecode dd pass, zeroed every round
+  uint32_t rng, mrg_bits;           // generator (0 Philox, 1 MRG32k3a), sample index bits
+  const uint32_t *mrg_jump;         // MRG32k3a jump table
 };
 
 __device__ __forceinline__ KParams batch_kparams(const BatchParams &B, const BatchDiag &D) {
@@ -59,6 +63,9 @@ __device__ __forceinline__ KParams batch_kparams(const BatchParams &B, const Bat
   P.thresh = B.thresh;
   P.partials = nullptr; P.counts = nullptr; P.queue = nullptr; P.queue_len = nullptr; P.queue_cap = 0;
   P.z_out = P.f_out = P.lp_out = nullptr; P.flag_out = nullptr;
+  P.rng = B.rng; P.mrg_bits = B.mrg_bits; P.mrg_jump = B.mrg_jump;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) P.mrg[i] = D.mrg[i];
   return P;
 }
 

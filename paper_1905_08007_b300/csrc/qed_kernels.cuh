@@ -34,6 +34,51 @@ __device__ __forceinline__ double u01(uint32_t hi, uint32_t lo) {
   return (double(x) + 0.5) * 2.220446049250313080847e-16;   // 2^-52
 }
 
+// ---------------------------------------------------------------------------
+// device: MRG32k3a (L'Ecuyer 1999; the paper's Calc 1 generator, Sec. 3)
+//   x1[n] = (1403580 x1[n-2] - 810728 x1[n-3]) mod m1,   m1 = 2^32 - 209
+//   x2[n] = (527612 x2[n-1] - 1370589 x2[n-3]) mod m2,   m2 = 2^32 - 22853
+//   z = (x1[n] - x2[n]) mod m1 (z = 0 -> m1), u = z * (double nearest 1/(m1+1)).
+// Sample s of a graph owns the 32 draws from position s * 2^5 of the
+// graph's stream; the host gives the stream's start state (position
+// seed * 2^127 + stream id * 2^96 from the all-12345 state) and a table of
+// the jump matrices A^(2^(5+k)), k = 0..63, of both recurrences.  A thread
+// jumps to its sample by the bits of s (one 3x3 product per bit, modulo m,
+// on the integer pipe), then steps the recurrences draw by draw.
+// ---------------------------------------------------------------------------
+#define QED_MRG_M1 4294967087ull
+#define QED_MRG_M2 4294944443ull
+
+// x mod m1 for any 64-bit x: 2^32 = 209 (mod m1), folded twice
+__device__ __forceinline__ uint32_t mrg_mod1(uint64_t x) {
+  uint64_t t = (x >> 32) * 209ull + (x & 0xffffffffull);      // < 2^40
+  t = (t >> 32) * 209ull + (t & 0xffffffffull);               // < 2^32 + 2^16 < 2 m1
+  return uint32_t(t >= QED_MRG_M1 ? t - QED_MRG_M1 : t);
+}
+// x mod m2 for any 64-bit x: 2^32 = 22853 (mod m2), folded twice
+__device__ __forceinline__ uint32_t mrg_mod2(uint64_t x) {
+  uint64_t t = (x >> 32) * 22853ull + (x & 0xffffffffull);    // < 2^47
+  t = (t >> 32) * 22853ull + (t & 0xffffffffull);             // < 2^32 + 2^30 < 2 m2
+  return uint32_t(t >= QED_MRG_M2 ? t - QED_MRG_M2 : t);
+}
+// v <- A v (mod m) for a row-major 3x3 matrix A read from the jump table
+template <int C>
+__device__ __forceinline__ void mrg_matvec(const uint32_t *__restrict__ A, uint32_t (&v)[3]) {
+  uint32_t r[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    uint64_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const uint64_t p = uint64_t(__ldg(A + 3 * i + k)) * v[k];
+      acc += C == 1 ? mrg_mod1(p) : mrg_mod2(p);              // three terms < 3 m
+    }
+    r[i] = C == 1 ? mrg_mod1(acc) : mrg_mod2(acc);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) v[i] = r[i];
+}
+
 struct KParams {
   const double *F;        // F(S), 2^N
   const double *G;        // F(S) / Deg(S), 2^N
@@ -52,7 +97,35 @@ struct KParams {
   // dump mode
   double *z_out, *f_out, *lp_out;
   uint8_t *flag_out;
+  // random numbers: rng 0 = Philox4x32-10, 1 = MRG32k3a (stream start state
+  // mrg[0..2] = x1, mrg[3..5] = x2; jump table [64][18]; sample indices
+  // below 2^mrg_bits)
+  uint32_t rng, mrg_bits;
+  uint32_t mrg[6];
+  const uint32_t *mrg_jump;
 };
+
+// The ND uniforms of sample s from MRG32k3a.
+template <int ND>
+__device__ __forceinline__ void mrg_draws(uint64_t s, const KParams &P, double (&u)[ND]) {
+  uint32_t a[3] = {P.mrg[0], P.mrg[1], P.mrg[2]}, b[3] = {P.mrg[3], P.mrg[4], P.mrg[5]};
+  for (uint32_t k = 0; k < P.mrg_bits; ++k) {
+    if ((s >> k) & 1ull) {
+      mrg_matvec<1>(P.mrg_jump + 18 * k, a);
+      mrg_matvec<2>(P.mrg_jump + 18 * k + 9, b);
+    }
+  }
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    // 810728 x1[n-3] < 2^20 m1 and 1370589 x2[n-3] < 2^21 m2: no wrap
+    const uint32_t p1 = mrg_mod1(1403580ull * a[1] + (QED_MRG_M1 << 20) - 810728ull * a[0]);
+    const uint32_t p2 = mrg_mod2(527612ull * b[2] + (QED_MRG_M2 << 21) - 1370589ull * b[0]);
+    a[0] = a[1]; a[1] = a[2]; a[2] = p1;
+    b[0] = b[1]; b[1] = b[2]; b[2] = p2;
+    const uint32_t z = p1 > p2 ? p1 - p2 : uint32_t(uint64_t(p1) + QED_MRG_M1 - p2);
+    u[d] = double(z) * 2.328306549295727688e-10;        // the double nearest 1 / (m1 + 1)
+  }
+}
 
 // Error model of the FP64 integrand: every monomial is computed to a few ulps
 // and the sum loses log2(sum|m| / |sum m|) bits, so the relative error is
@@ -75,11 +148,15 @@ __device__ __forceinline__ double draw_point(uint64_t s, const KParams &P, const
                                              double *logt_out = nullptr) {
   constexpr int ND = 2 * (N - 1);
   double u[ND];
+  if (P.rng == 1) {
+    mrg_draws<ND>(s, P, u);
+  } else {
 #pragma unroll
-  for (int b = 0; b < (ND + 1) / 2; ++b) {
-    U4 w = philox4x32_10(U4{uint32_t(s), uint32_t(s >> 32), P.stream, uint32_t(b)}, P.key0, P.key1);
-    u[2 * b] = u01(w.x, w.y);
-    if (2 * b + 1 < ND) u[2 * b + 1] = u01(w.z, w.w);
+    for (int b = 0; b < (ND + 1) / 2; ++b) {
+      U4 w = philox4x32_10(U4{uint32_t(s), uint32_t(s >> 32), P.stream, uint32_t(b)}, P.key0, P.key1);
+      u[2 * b] = u01(w.x, w.y);
+      if (2 * b + 1 < ND) u[2 * b + 1] = u01(w.z, w.w);
+    }
   }
   const uint32_t full = (1u << N) - 1u;
   uint32_t S = full;

@@ -54,9 +54,24 @@ struct VmCode {
 // lane is double).
 #define VM_E_FLOOR 1e-30f
 
+// Interval of the FP64 interval pass (Sec. 3 controls the round-off of the
+// numerical subtraction with interval arithmetic): every operation rounds
+// its lower end down and its upper end up, so [lo, hi] encloses the exact
+// value of the program's arithmetic at the point (with the program's FP64
+// constants), whatever the cancellation between forest terms.
+struct __align__(16) ivl {
+  double lo, hi;
+  __host__ __device__ ivl() : lo(0.0), hi(0.0) {}
+  __host__ __device__ explicit ivl(double x) : lo(x), hi(x) {}
+  __host__ __device__ ivl(double l, double h) : lo(l), hi(h) {}
+};
+
 template <class R> struct VmE;
 template <> struct VmE<double> { typedef float T; };
 template <> struct VmE<dd> { typedef double T; };
+template <> struct VmE<ivl> { typedef float T; };   // not stored: an interval bounds its own error
+template <class R> struct VmHasE { static constexpr bool value = true; };
+template <> struct VmHasE<ivl> { static constexpr bool value = false; };
 
 __device__ __forceinline__ double vm_mag(double x) { return fabs(x); }
 __device__ __forceinline__ double vm_mag(dd x) { return fabs(x.hi + x.lo); }
@@ -95,8 +110,44 @@ __device__ __forceinline__ dd vm_fma(dd a, dd b, dd c) {
   const dd s = two_sum(p, c.hi);
   return quick_two_sum(s.hi, __dadd_rn(__dadd_rn(s.lo, pl), c.lo));
 }
+// a * b + c in interval arithmetic: the bounds of the product are the
+// products of the ends picked by the signs of a and b (all four candidates
+// only where both straddle zero), each fused with the matching end of c and
+// rounded outward (down for lo, up for hi) by the directed-rounding FMA.
+// A NaN end (a product of zero and an infinite end) fails every sign test
+// and propagates, and the point is flagged.
+__device__ __forceinline__ double vm_mag(ivl x) { return fmax(fabs(x.lo), fabs(x.hi)); }
+__device__ __forceinline__ ivl vm_fma(ivl a, ivl b, ivl c) {
+  double l, h;
+  if (b.lo >= 0.0) {
+    if (a.lo >= 0.0)      { l = __fma_rd(a.lo, b.lo, c.lo); h = __fma_ru(a.hi, b.hi, c.hi); }
+    else if (a.hi <= 0.0) { l = __fma_rd(a.lo, b.hi, c.lo); h = __fma_ru(a.hi, b.lo, c.hi); }
+    else                  { l = __fma_rd(a.lo, b.hi, c.lo); h = __fma_ru(a.hi, b.hi, c.hi); }
+  } else if (b.hi <= 0.0) {
+    if (a.lo >= 0.0)      { l = __fma_rd(a.hi, b.lo, c.lo); h = __fma_ru(a.lo, b.hi, c.hi); }
+    else if (a.hi <= 0.0) { l = __fma_rd(a.hi, b.hi, c.lo); h = __fma_ru(a.lo, b.lo, c.hi); }
+    else                  { l = __fma_rd(a.hi, b.lo, c.lo); h = __fma_ru(a.lo, b.lo, c.hi); }
+  } else if (b.lo < 0.0 && b.hi > 0.0) {
+    if (a.lo >= 0.0)      { l = __fma_rd(a.hi, b.lo, c.lo); h = __fma_ru(a.hi, b.hi, c.hi); }
+    else if (a.hi <= 0.0) { l = __fma_rd(a.lo, b.hi, c.lo); h = __fma_ru(a.lo, b.lo, c.hi); }
+    else {
+      l = fmin(__fma_rd(a.lo, b.hi, c.lo), __fma_rd(a.hi, b.lo, c.lo));
+      h = fmax(__fma_ru(a.lo, b.lo, c.hi), __fma_ru(a.hi, b.hi, c.hi));
+    }
+  } else {
+    l = h = __longlong_as_double(0x7ff8000000000000ll);   // b has a NaN end
+  }
+  if (!(a.lo <= a.hi)) l = h = __longlong_as_double(0x7ff8000000000000ll);
+  return ivl(l, h);
+}
 __device__ __forceinline__ double vm_rcp(double a) { return 1.0 / a; }
 __device__ __forceinline__ dd vm_rcp(dd a) { return dd(1.0) / a; }
+// 1 / [lo, hi] = [1/hi, 1/lo] (rounded outward) when the interval excludes
+// zero, else everything
+__device__ __forceinline__ ivl vm_rcp(ivl a) {
+  if (a.lo > 0.0 || a.hi < 0.0) return ivl(__drcp_rd(a.hi), __drcp_ru(a.lo));
+  return ivl(-__longlong_as_double(0x7ff0000000000000ll), __longlong_as_double(0x7ff0000000000000ll));
+}
 template <class E> __device__ __forceinline__ E vm_abs_e(double m);
 template <> __device__ __forceinline__ float vm_abs_e<float>(double m) { return float(m); }
 template <> __device__ __forceinline__ double vm_abs_e<double>(double m) { return m; }
@@ -144,9 +195,10 @@ __host__ __device__ __forceinline__ size_t vm_value_bytes(int n_kon, int n_regs,
 }
 template <class R, int P>
 __host__ __device__ __forceinline__ size_t vm_smem_bytes(int n_kon, int n_regs, int T) {
-  static_assert(2 * sizeof(typename VmE<R>::T) == sizeof(R), "e lane is half the value width");
+  static_assert(!VmHasE<R>::value || 2 * sizeof(typename VmE<R>::T) == sizeof(R),
+                "e lane is half the value width");
   const size_t v = vm_value_bytes<R, P>(n_kon, n_regs, T);
-  return v + v / 2;
+  return VmHasE<R>::value ? v + v / 2 : v;
 }
 
 template <class R, int P>
@@ -166,7 +218,7 @@ struct VmFrame {
     for (int i = threadIdx.x; i < C.n_kon * P; i += blockDim.x) {
       const double c = C.kon[i / P];
       k[i] = R(c);
-      kabs[i] = E(fabs(c));
+      if (VmHasE<R>::value) kabs[i] = E(fabs(c));
     }
     const uint32_t v0 = uint32_t(C.n_kon) * P * sizeof(R);
     vs = uint32_t(T) * P * sizeof(R);
@@ -177,13 +229,17 @@ struct VmFrame {
   __device__ __forceinline__ void put(uint32_t r, const R (&v)[P], const E (&e)[P]) {
     const uint32_t vo = vt + r * vs;
     VmVec<R, P>::st(sm + vo, v);
-    VmVec<E, P>::st(sm + ex + (vo >> 1), e);
+    if (VmHasE<R>::value) VmVec<E, P>::st(sm + ex + (vo >> 1), e);
   }
   __device__ __forceinline__ void get(uint32_t a, R (&v)[P], E (&e)[P]) const {
     const uint32_t i = a & (VM_KFLAG - 1u);
     const uint32_t vo = a >= VM_KFLAG ? i * uint32_t(P * sizeof(R)) : vt + a * vs;
     VmVec<R, P>::ld(sm + vo, v);
-    VmVec<E, P>::ld(sm + ex + (vo >> 1), e);
+    if (VmHasE<R>::value) VmVec<E, P>::ld(sm + ex + (vo >> 1), e);
+    else {
+#pragma unroll
+      for (int p = 0; p < P; ++p) e[p] = E(0);
+    }
   }
 
   // One instruction whose operands are already loaded: compute, special,
@@ -198,7 +254,7 @@ struct VmFrame {
         const R X = xa ? va[p] : acc[p], O = xa ? acc[p] : va[p];
         const E eX = xa ? ea[p] : ae[p], eO = xa ? ae[p] : ea[p];
         acc[p] = vm_fma(X, vb[p], zo ? O : R(0.0));
-        ae[p] = eX * eb[p] + (zo ? eO : E(0));
+        if (VmHasE<R>::value) ae[p] = eX * eb[p] + (zo ? eO : E(0));
       }
       const uint32_t d = hi >> 6;
       put(d ? d : spare, acc, ae);
@@ -216,7 +272,7 @@ struct VmFrame {
         const R X = xa ? va[p] : acc[p], O = xa ? acc[p] : va[p];
         const E eX = xa ? ea[p] : ae[p], eO = xa ? ae[p] : ea[p];
         acc[p] = vm_fma(X, vb[p], zo ? O : R(0.0));
-        ae[p] = eX * eb[p] + (zo ? eO : E(0));
+        if (VmHasE<R>::value) ae[p] = eX * eb[p] + (zo ? eO : E(0));
       }
     }
     const uint32_t sp = (hi >> 2) & 7u;
@@ -225,6 +281,8 @@ struct VmFrame {
 #pragma unroll
       for (int p = 0; p < P; ++p) {
         if (sp == VM_SP_RCP) { acc[p] = vm_rcp(acc[p]); ae[p] = vm_abs_e<E>(vm_mag(acc[p])); }
+        else if (!VmHasE<R>::value) {
+        }
         else if (sp == VM_SP_ABS) ae[p] = vm_abs_e<E>(vm_mag(acc[p]));
         else if (sp == VM_SP_ACCW) {
           // range guard of the FP32 lane: a block value whose absolute sum
@@ -632,13 +690,78 @@ __global__ void __launch_bounds__(256) k_batch_vm_dd(BatchParams B) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// interval pass (Sec. 3: interval arithmetic with different precisions
+// removes the round-off of the numerical subtraction).  Each point is
+// evaluated in FP64 interval arithmetic; its value is the midpoint of
+// [lo, hi], accepted when both ends have one sign and
+// hi - lo <= 2 thresh min(|lo|, |hi|), which bounds the relative error of the
+// midpoint against every value in the interval by thresh.  Other points go
+// to the flagged queue and are re-evaluated in double-double (k_redo_dd_vm).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool ivl_accept(ivl f, double thresh, double &mid) {
+  mid = 0.5 * f.lo + 0.5 * f.hi;
+  const double m = fmin(fabs(f.lo), fabs(f.hi));
+  return (f.lo > 0.0 || f.hi < 0.0) && (f.hi - f.lo) <= 2.0 * thresh * m;
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) k_eval_vm_ivl(const double *__restrict__ zin, uint64_t n,
+                                                     double *__restrict__ lo, double *__restrict__ hi, VmCode C) {
+  extern __shared__ __align__(16) unsigned char vsm[];
+  VmFrame<ivl, 1> fr;
+  fr.setup(C, vsm);
+  const uint64_t nth = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += nth) {
+    ivl z[1][N], f[1];
+    double ab[1];
+#pragma unroll
+    for (int L = 0; L < N; ++L) z[0][L] = ivl(zin[i * N + L]);
+    fr.template eval<N>(C, z, f, ab);
+    lo[i] = f[0].lo;
+    hi[i] = f[0].hi;
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) k_integrate_vm_ivl(KParams K, VmCode C) {
+  extern __shared__ __align__(16) unsigned char vsm[];
+  VmFrame<ivl, 1> fr;
+  fr.setup(C, vsm);
+  KSum sw, sw2;
+  unsigned long long nflag = 0;
+  const uint64_t nth = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < K.n; i += nth) {
+    double z[N];
+    const double lp = draw_point<N>(K.begin + i, K, K.F, K.G, K.invdeg, z);
+    ivl zi[1][N], f[1];
+    double ab[1];
+#pragma unroll
+    for (int L = 0; L < N; ++L) zi[0][L] = ivl(z[L]);
+    fr.template eval<N>(C, zi, f, ab);
+    double mid;
+    const bool ok = ivl_accept(f[0], K.thresh, mid);
+    const double w = mid * exp(-lp);
+    if (!ok || !isfinite(w)) {
+      ++nflag;
+      const unsigned int slot = atomicAdd(K.queue_len, 1u);
+      if (slot < K.queue_cap) K.queue[slot] = i;
+    } else {
+      sw.add(w);
+      sw2.add(w * w);
+    }
+  }
+  block_reduce_store(sw, sw2, nflag, 0ull, K.partials, K.counts, blockIdx.x);
+}
+
 // Kernel table of the bytecode path for one line count N and P points per
 // thread in the FP64 kernels.
 struct VmKernelSet {
-  const void *integrate, *redo, *dump, *eval, *grad, *batch64, *batchdd, *grad_dd;
+  const void *integrate, *redo, *dump, *eval, *grad, *batch64, *batchdd, *grad_dd, *eval_ivl, *integrate_ivl;
 };
 #define QED_VM_KSET(N, P)                                                                                       \
   VmKernelSet{(const void *)k_integrate_vm<N, P>, (const void *)k_redo_dd_vm<N>, (const void *)k_dump_vm<N, P>, \
               (const void *)k_eval_vm<N, P>, (const void *)k_pdf_grad_vm<N, P>,                                 \
               (const void *)k_batch_vm_fp64<N, P>, (const void *)k_batch_vm_dd<N>,                              \
-              (const void *)k_pdf_grad_dd_vm<N>}
+              (const void *)k_pdf_grad_dd_vm<N>, (const void *)k_eval_vm_ivl<N>,                                \
+              (const void *)k_integrate_vm_ivl<N>}

@@ -44,6 +44,77 @@ static int set_err(int code, const std::string &msg) { g_err = msg; return code;
 extern "C" const char *qed_last_error(void) { return g_err.c_str(); }
 
 // ---------------------------------------------------------------------------
+// MRG32k3a jump-ahead on the host (L'Ecuyer 1999; L'Ecuyer, Simard, Chen,
+// Kelton 2002 for jumps by matrix powers): the one-step matrices of both
+// recurrences, their powers A^(2^k) for k = 0..190 by repeated squaring
+// (exact products in 128-bit integers), the start state of a (seed, stream)
+// at position seed * 2^127 + stream * 2^96 from the all-12345 state, and
+// the device table of A^(2^(5+k)), k = 0..63, the jumps by sample index.
+// ---------------------------------------------------------------------------
+namespace mrg {
+constexpr uint64_t M1 = 4294967087ull, M2 = 4294944443ull;
+struct Mat { uint64_t a[9]; };
+static Mat mul(const Mat &x, const Mat &y, uint64_t m) {
+  Mat r;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      unsigned __int128 acc = 0;
+      for (int k = 0; k < 3; ++k) acc += (unsigned __int128)x.a[3 * i + k] * y.a[3 * k + j];
+      r.a[3 * i + j] = uint64_t(acc % m);
+    }
+  return r;
+}
+static void apply(const Mat &x, uint64_t (&v)[3], uint64_t m) {
+  uint64_t r[3];
+  for (int i = 0; i < 3; ++i) {
+    unsigned __int128 acc = 0;
+    for (int k = 0; k < 3; ++k) acc += (unsigned __int128)x.a[3 * i + k] * v[k];
+    r[i] = uint64_t(acc % m);
+  }
+  for (int i = 0; i < 3; ++i) v[i] = r[i];
+}
+// powers()[c][k] = A_c^(2^k), c = 0 (x1, mod m1) or 1 (x2, mod m2)
+static const std::vector<Mat> *powers() {
+  static const std::vector<Mat> *P = [] {
+    auto *t = new std::vector<Mat>[2];
+    const Mat a1 = {{0, 1, 0, 0, 0, 1, M1 - 810728ull, 1403580ull, 0}};
+    const Mat a2 = {{0, 1, 0, 0, 0, 1, M2 - 1370589ull, 0, 527612ull}};
+    t[0].push_back(a1);
+    t[1].push_back(a2);
+    for (int k = 1; k < 191; ++k) {
+      t[0].push_back(mul(t[0].back(), t[0].back(), M1));
+      t[1].push_back(mul(t[1].back(), t[1].back(), M2));
+    }
+    return t;
+  }();
+  return P;
+}
+static void stream_start(uint64_t seed, uint32_t stream, uint32_t out[6]) {
+  const std::vector<Mat> *P = powers();
+  uint64_t v1[3] = {12345, 12345, 12345}, v2[3] = {12345, 12345, 12345};
+  for (int j = 0; j < 64; ++j)
+    if (seed >> j & 1) { apply(P[0][127 + j], v1, M1); apply(P[1][127 + j], v2, M2); }
+  for (int j = 0; j < 32; ++j)
+    if (stream >> j & 1) { apply(P[0][96 + j], v1, M1); apply(P[1][96 + j], v2, M2); }
+  for (int i = 0; i < 3; ++i) { out[i] = uint32_t(v1[i]); out[3 + i] = uint32_t(v2[i]); }
+}
+static std::vector<uint32_t> jump_table() {
+  const std::vector<Mat> *P = powers();
+  std::vector<uint32_t> t(64 * 18);
+  for (int k = 0; k < 64; ++k)
+    for (int i = 0; i < 9; ++i) {
+      t[18 * k + i] = uint32_t(P[0][5 + k].a[i]);
+      t[18 * k + 9 + i] = uint32_t(P[1][5 + k].a[i]);
+    }
+  return t;
+}
+// sample indices below 2^bits cover [0, end)
+static uint32_t index_bits(uint64_t end) {
+  return end <= 1 ? 1u : uint32_t(64 - __builtin_clzll(end - 1));
+}
+}  // namespace mrg
+
+// ---------------------------------------------------------------------------
 // kernel tables (one translation unit per generated graph defines qed_kset_<id>)
 // ---------------------------------------------------------------------------
 #define QED_DECL_KSET(id, lines) extern const KernelSet qed_kset_##id;
@@ -93,6 +164,9 @@ struct qed_ctx {
   struct BatchPlan *plan = nullptr;   // qed_integrate_batch's cached set-up
   int vm_threads = 128;      // threads per block of the FP64 interpreter kernels
   int vm_points = 1;         // points per thread of the FP64 interpreter kernels
+  int flag_rule = QED_FLAG_ESTIMATE;   // which points go to the double-double pass
+  int rng = QED_RNG_PHILOX;  // generator of the sample points
+  uint32_t *mrg_jump = nullptr;   // MRG32k3a jump table on the device
 };
 
 struct qed_diag {
@@ -193,6 +267,9 @@ extern "C" int qed_ctx_create(int device, uint64_t flags, qed_ctx **out) {
   CUDA_TRY(cudaEventCreate(&c->evk2));
   int rc = ensure_scratch(c, 8 * c->sms);
   if (rc) return rc;
+  const std::vector<uint32_t> jt = mrg::jump_table();
+  CUDA_TRY(cudaMalloc(&c->mrg_jump, jt.size() * sizeof(uint32_t)));
+  CUDA_TRY(cudaMemcpy(c->mrg_jump, jt.data(), jt.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
   *out = c;
   return QED_OK;
 }
@@ -206,6 +283,7 @@ extern "C" int qed_ctx_destroy(qed_ctx *c) {
   if (c->counts) cudaFree(c->counts);
   if (c->queue) cudaFree(c->queue);
   if (c->queue_len) cudaFree(c->queue_len);
+  if (c->mrg_jump) cudaFree(c->mrg_jump);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->evk0) cudaEventDestroy(c->evk0);
@@ -237,6 +315,20 @@ extern "C" int qed_ctx_set_vm(qed_ctx *c, int threads, int points) {
   if (points != 1 && points != 2) return set_err(QED_EINVAL, "points per thread must be 1 or 2");
   c->vm_threads = threads;
   c->vm_points = points;
+  return QED_OK;
+}
+
+extern "C" int qed_ctx_set_rng(qed_ctx *c, int rng) {
+  if (!c) return set_err(QED_EINVAL, "ctx is NULL");
+  if (rng != QED_RNG_PHILOX && rng != QED_RNG_MRG32K3A) return set_err(QED_EINVAL, "unknown generator");
+  c->rng = rng;
+  return QED_OK;
+}
+
+extern "C" int qed_ctx_set_flag_rule(qed_ctx *c, int rule) {
+  if (!c) return set_err(QED_EINVAL, "ctx is NULL");
+  if (rule != QED_FLAG_ESTIMATE && rule != QED_FLAG_INTERVAL) return set_err(QED_EINVAL, "unknown flag rule");
+  c->flag_rule = rule;
   return QED_OK;
 }
 
@@ -496,6 +588,12 @@ static KParams base_params(const qed_diag *d, uint64_t begin, uint64_t n, uint64
   P.key0 = uint32_t(seed); P.key1 = uint32_t(seed >> 32);
   P.stream = d->stream_id;
   P.thresh = d->ctx->thresh;
+  P.rng = uint32_t(d->ctx->rng);
+  if (P.rng == QED_RNG_MRG32K3A) {
+    P.mrg_bits = mrg::index_bits(begin + n);
+    P.mrg_jump = d->ctx->mrg_jump;
+    mrg::stream_start(seed, d->stream_id, P.mrg);
+  }
   return P;
 }
 
@@ -512,12 +610,16 @@ struct VmLaunch {
   size_t smem = 0;
   VmCode code;
 };
-static int vm_launch(const qed_ctx *c, const qed_ctx::VmProg &pr, const void *fn, bool dd_frame, int threads,
+// frame: 0 = FP64 (the context's points per thread), 1 = double-double,
+// 2 = FP64 interval
+static int vm_launch(const qed_ctx *c, const qed_ctx::VmProg &pr, const void *fn, int frame, int threads,
                      VmLaunch &L) {
   L.code = VmCode{pr.d_ins, pr.d_kon, pr.n_kon, pr.n_regs};
   const size_t cap = 220 * 1024;       // dynamic part; the kernels' static shared memory is a few KB
+  const bool dd_frame = frame != 0;    // both wide frames take the occupancy search below
   auto bytes = [&](int t) {
-    if (dd_frame) return vm_smem_bytes<dd, 1>(pr.n_kon, pr.n_regs, t);
+    if (frame == 2) return vm_smem_bytes<ivl, 1>(pr.n_kon, pr.n_regs, t);
+    if (frame == 1) return vm_smem_bytes<dd, 1>(pr.n_kon, pr.n_regs, t);
     return c->vm_points == 2 ? vm_smem_bytes<double, 2>(pr.n_kon, pr.n_regs, t)
                              : vm_smem_bytes<double, 1>(pr.n_kon, pr.n_regs, t);
   };
@@ -526,8 +628,8 @@ static int vm_launch(const qed_ctx *c, const qed_ctx::VmProg &pr, const void *fn
   if (bytes(T) > cap) return set_err(QED_EINVAL, "program " + pr.name + " needs more shared memory than a block has");
   int occ = 0;
   if (dd_frame) {
-    // the double-double frame (24 bytes per register and thread) limits an
-    // SM to a few warps: take the block size, 32 to 256 threads, that keeps
+    // the double-double frame (24 bytes per register and thread; an
+    // interval 16) limits an SM to a few warps: take the block size, 32 to 256 threads, that keeps
     // the most threads resident (the smaller one on a tie), e.g. one block
     // of 128 rather than one of 64 for the largest four-loop programs
     int best = 0;
@@ -560,8 +662,10 @@ static int integrate_range_vm(qed_diag *d, uint64_t begin, uint64_t n, uint64_t 
   const VmKernelSet &K = vm_kernels(d);
   const auto &pr = c->vm[d->vm];
   VmLaunch L1, L2;
-  int rc = vm_launch(c, pr, K.integrate, false, c->vm_threads, L1);
-  if (!rc) rc = vm_launch(c, pr, K.redo, true, 64, L2);
+  const bool interval = c->flag_rule == QED_FLAG_INTERVAL;
+  const void *kint = interval ? K.integrate_ivl : K.integrate;
+  int rc = vm_launch(c, pr, kint, interval ? 2 : 0, interval ? 64 : c->vm_threads, L1);
+  if (!rc) rc = vm_launch(c, pr, K.redo, 1, 64, L2);
   if (!rc) rc = ensure_scratch(c, std::max(L1.blocks, L2.blocks));
   if (rc) return rc;
   qed_result r;
@@ -577,7 +681,7 @@ static int integrate_range_vm(qed_diag *d, uint64_t begin, uint64_t n, uint64_t 
     CUDA_TRY(cudaMemsetAsync(c->queue_len, 0, sizeof(unsigned int), c->stream));
     void *args[] = {&P, &L1.code};
     CUDA_TRY(cudaEventRecord(c->evk0, c->stream));
-    if ((rc = launch(K.integrate, L1.blocks, L1.threads, L1.smem, c->stream, args))) return rc;
+    if ((rc = launch(kint, L1.blocks, L1.threads, L1.smem, c->stream, args))) return rc;
     CUDA_TRY(cudaEventRecord(c->evk1, c->stream));
     ++r.launches;
     if ((rc = fold(c, L1.blocks, &r, true))) return rc;
@@ -648,6 +752,9 @@ extern "C" int qed_integrate_range(qed_diag *d, uint64_t begin, uint64_t n, uint
   qed_ctx *c = d->ctx;
   CUDA_TRY(cudaSetDevice(c->device));
   if (d->vm >= 0) return integrate_range_vm(d, begin, n, seed, out);
+  if (c->flag_rule == QED_FLAG_INTERVAL)
+    return set_err(QED_EINVAL, "the interval rule evaluates bytecode programs: load the graph on a "
+                               "QED_CTX_PREFER_PROGRAMS context");
   const KernelSet &K = *g_kernels[d->fid];
   const int threads = c->threads;
   const int blocks = c->blocks > 0 ? c->blocks : 4 * c->sms;
@@ -723,7 +830,7 @@ extern "C" int qed_dump_points(qed_diag *d, uint64_t begin, uint64_t n, uint64_t
   P.z_out = z_dev; P.f_out = f_dev; P.lp_out = lp_dev; P.flag_out = flag_dev;
   if (d->vm >= 0) {
     VmLaunch L;
-    int rc = vm_launch(c, c->vm[d->vm], vm_kernels(d).dump, false, c->vm_threads, L);
+    int rc = vm_launch(c, c->vm[d->vm], vm_kernels(d).dump, 0, c->vm_threads, L);
     if (rc) return rc;
     const int blocks = int(std::max<uint64_t>(1, std::min<uint64_t>((n + L.threads - 1) / L.threads, uint64_t(L.blocks))));
     void *args[] = {&P, &L.code};
@@ -747,7 +854,7 @@ extern "C" int qed_eval_points(qed_diag *d, const double *z_dev, uint64_t n, int
   if (d->vm >= 0) {
     VmLaunch L;
     const void *fn = vm_kernels(d).eval;
-    int rc = vm_launch(c, c->vm[d->vm], fn, prec == 1, prec == 1 ? 64 : c->vm_threads, L);
+    int rc = vm_launch(c, c->vm[d->vm], fn, prec == 1 ? 1 : 0, prec == 1 ? 64 : c->vm_threads, L);
     if (rc) return rc;
     const int blocks = int(std::max<uint64_t>(1, std::min<uint64_t>((n + L.threads - 1) / L.threads, uint64_t(L.blocks))));
     void *args[] = {(void *)&z_dev, &n, &prec, &f_dev, &L.code};
@@ -760,6 +867,25 @@ extern "C" int qed_eval_points(qed_diag *d, const double *z_dev, uint64_t n, int
   void *args[] = {(void *)&z_dev, &n, &prec, &f_dev};
   int rc = launch(g_kernels[d->fid]->eval, blocks, threads, 0, c->stream, args);
   if (rc) return rc;
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return QED_OK;
+}
+
+extern "C" int qed_eval_interval(qed_diag *d, const double *z_dev, uint64_t n, double *lo_dev, double *hi_dev) {
+  if (!d || !z_dev || !lo_dev || !hi_dev) return set_err(QED_EINVAL, "bad argument");
+  if (d->vm < 0)
+    return set_err(QED_EINVAL, "interval arithmetic runs on bytecode programs: load the graph on a "
+                               "QED_CTX_PREFER_PROGRAMS context");
+  if (n == 0) return QED_OK;
+  qed_ctx *c = d->ctx;
+  CUDA_TRY(cudaSetDevice(c->device));
+  VmLaunch L;
+  const void *fn = vm_kernels(d).eval_ivl;
+  int rc = vm_launch(c, c->vm[d->vm], fn, 2, 64, L);
+  if (rc) return rc;
+  const int blocks = int(std::max<uint64_t>(1, std::min<uint64_t>((n + L.threads - 1) / L.threads, uint64_t(L.blocks))));
+  void *args[] = {(void *)&z_dev, &n, &lo_dev, &hi_dev, &L.code};
+  if ((rc = launch(fn, blocks, L.threads, L.smem, c->stream, args))) return rc;
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   return QED_OK;
 }
@@ -885,6 +1011,8 @@ struct BatchPlan {
   size_t smem = 0, smem2 = 0;
   bool use_graph = true;
   cudaStream_t user_stream = 0;
+  int rng = 0;
+  uint32_t mrg_bits = 0;
   // resources: dev = {graph descriptors, items, next-item counters, FP64
   // partials, FP64 counts, dd partials, dd counts, flagged lists}
   void *dev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -901,13 +1029,14 @@ struct BatchPlan {
     return diags == o.diags && seed == o.seed && thresh == o.thresh && n_items == o.n_items &&
            list_cap == o.list_cap && dd_tiles == o.dd_tiles && kern1 == o.kern1 && kern2 == o.kern2 &&
            grid1 == o.grid1 && grid2 == o.grid2 && thr1 == o.thr1 && thr2 == o.thr2 && smem == o.smem &&
-           smem2 == o.smem2 && use_graph == o.use_graph && user_stream == o.user_stream;
+           smem2 == o.smem2 && use_graph == o.use_graph && user_stream == o.user_stream && rng == o.rng &&
+           mrg_bits == o.mrg_bits;
   }
   BatchPlan() = default;
   BatchPlan(const BatchPlan &key) : diags(key.diags), seed(key.seed), thresh(key.thresh), n_items(key.n_items),
       list_cap(key.list_cap), dd_tiles(key.dd_tiles), kern1(key.kern1), kern2(key.kern2), grid1(key.grid1),
       grid2(key.grid2), thr1(key.thr1), thr2(key.thr2), smem(key.smem), smem2(key.smem2),
-      use_graph(key.use_graph), user_stream(key.user_stream) {}
+      use_graph(key.use_graph), user_stream(key.user_stream), rng(key.rng), mrg_bits(key.mrg_bits) {}
   BatchPlan &operator=(const BatchPlan &) = delete;
   ~BatchPlan() {
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -961,6 +1090,7 @@ struct BatchPlan {
     B.lists = (uint32_t *)dev[7]; B.list_cap = list_cap;
     B.part_dd = (double *)dev[5]; B.cnt_dd = (unsigned long long *)dev[6];
     B.dd_tiles = dd_tiles; B.next_tile = (unsigned int *)dev[2] + 1;
+    B.rng = uint32_t(rng); B.mrg_bits = mrg_bits; B.mrg_jump = c->mrg_jump;
     st = user_stream;
     if (use_graph) {
       if (st == 0) { CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own_stream = true; }
@@ -996,6 +1126,7 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
   const int list_div = o.list_div > 0 ? o.list_div : 16;
   if (chunk > (uint64_t(1) << 31)) return set_err(QED_EINVAL, "chunk must be <= 2^31");
   if (o.policy != 0 && o.policy != 1) return set_err(QED_EINVAL, "policy must be 0 or 1");
+  if (c->flag_rule != QED_FLAG_ESTIMATE) return set_err(QED_EINVAL, "the batched path flags by the estimate rule");
   CUDA_TRY(cudaSetDevice(c->device));
   // items per round (all rounds the same size so one captured graph serves all)
   const uint64_t per_round = (total + rounds - 1) / rounds;
@@ -1025,8 +1156,8 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
     const VmKernelSet &K = vm_kernels(d[0]);
     kern1 = K.batch64;
     kern2 = K.batchdd;
-    int rc = vm_launch(c, big, kern1, false, c->vm_threads, L1);
-    if (!rc) rc = vm_launch(c, big, kern2, true, 64, L2);
+    int rc = vm_launch(c, big, kern1, 0, c->vm_threads, L1);
+    if (!rc) rc = vm_launch(c, big, kern2, 1, 64, L2);
     if (rc) return rc;
     smem = L1.smem; smem2 = L2.smem; thr1 = L1.threads; thr2 = L2.threads;
   }
@@ -1044,6 +1175,14 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
   key.seed = seed; key.thresh = c->thresh; key.n_items = n_items; key.list_cap = list_cap; key.dd_tiles = dd_tiles;
   key.kern1 = kern1; key.kern2 = kern2; key.grid1 = grid1; key.grid2 = grid2; key.thr1 = thr1; key.thr2 = thr2;
   key.smem = smem; key.smem2 = smem2; key.use_graph = o.use_graph >= 0; key.user_stream = c->stream;
+  key.rng = c->rng;
+  if (c->rng == QED_RNG_MRG32K3A) {
+    // every sample index of the call is below counter_base + rounds x items
+    // x chunk; rounded up to a multiple of 8 bits so that the captured round
+    // is rebuilt rarely as the counters grow from call to call
+    const uint64_t end = o.counter_base + uint64_t(rounds) * n_items * chunk;
+    key.mrg_bits = std::min<uint32_t>(64u, (mrg::index_bits(end) + 7u) & ~7u);
+  }
   if (!c->plan || !c->plan->same_shape(key)) {
     drop_plan(c);
     BatchPlan *P = new BatchPlan(key);
@@ -1058,6 +1197,9 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
     hd[g].F = d[g]->d_tab; hd[g].G = d[g]->d_tab + M; hd[g].inv = d[g]->d_tab + 2 * M; hd[g].off = d[g]->d_tab + 3 * M;
     hd[g].logZ = d[g]->logZ; hd[g].stream = d[g]->stream_id; hd[g].fid = d[g]->fid; hd[g].N = d[g]->N; hd[g].pad = 0;
     hd[g].vins = nullptr; hd[g].vkon = nullptr; hd[g].vnk = 0; hd[g].vnr = 0;
+    std::memset(hd[g].mrg, 0, sizeof hd[g].mrg);
+    hd[g].pad2[0] = hd[g].pad2[1] = 0;
+    if (c->rng == QED_RNG_MRG32K3A) mrg::stream_start(seed, d[g]->stream_id, hd[g].mrg);
     if (d[g]->vm >= 0) {
       const auto &pr = c->vm[d[g]->vm];
       hd[g].vins = pr.d_ins; hd[g].vkon = pr.d_kon; hd[g].vnk = pr.n_kon; hd[g].vnr = pr.n_regs;
@@ -1236,8 +1378,8 @@ extern "C" int qed_pdf_grad(qed_diag *d, uint64_t begin, uint64_t n, uint64_t se
   size_t smem = table_smem(N), smem2 = smem;
   VmLaunch L, L2;
   if (vm) {
-    int rc = vm_launch(c, c->vm[d->vm], vm_kernels(d).grad, false, c->vm_threads, L);
-    if (!rc) rc = vm_launch(c, c->vm[d->vm], vm_kernels(d).grad_dd, true, 64, L2);
+    int rc = vm_launch(c, c->vm[d->vm], vm_kernels(d).grad, 0, c->vm_threads, L);
+    if (!rc) rc = vm_launch(c, c->vm[d->vm], vm_kernels(d).grad_dd, 1, 64, L2);
     if (rc) return rc;
     blocks = L.blocks; threads = L.threads; smem = L.smem;
     blocks2 = L2.blocks; threads2 = L2.threads; smem2 = L2.smem;
@@ -1426,6 +1568,7 @@ extern "C" int qed_integrate_range_noalloc(qed_diag *d, uint64_t begin, uint64_t
   if (!d || !out) return set_err(QED_EINVAL, "diag/out is NULL");
   qed_ctx *c = d->ctx;
   if (d->vm >= 0) return set_err(QED_EINVAL, "qed_integrate_range_noalloc: compiled integrands only (this graph uses a bytecode program)");
+  if (c->flag_rule != QED_FLAG_ESTIMATE) return set_err(QED_EINVAL, "qed_integrate_range_noalloc: estimate rule only");
   const int threads = c->threads;
   const int blocks = c->blocks > 0 ? c->blocks : 4 * c->sms;
   if (blocks > QED_NOALLOC_MAX_BLOCKS)
