@@ -315,7 +315,7 @@ def run_native(args):
     torch.cuda.set_device(local)
     import paper_1905_08007_b300 as q
     from paper_1905_08007_b300.tune import tune
-    ctx = q.Context(local, threshold=args.threshold)
+    ctx = q.Context(local, threshold=args.threshold, rng=args.rng)
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream)
     graphs, mw = graph_set(q, args.order)
@@ -453,6 +453,7 @@ def run_native(args):
                                "persistent batched kernel (4 CUDA-graph rounds per step)",
                    "loops": args.order, "graphs": len(graphs), "samples_per_step": total, "seed": args.seed, "l2_flush": True,
                    "flag_threshold": args.threshold, "deg": "calibrated" if args.calibrate else "rule",
+                   "rng": {"philox": "Philox4x32-10 (Calc 2)", "mrg32k3a": "MRG32k3a (Calc 1)"}[args.rng],
                    "launch": {"items_per_round": n_items, "chunk": chunk,
                               **({"vm_threads": ctx.vm_shape[0], "vm_points": ctx.vm_shape[1]} if args.order >= 4
                                  else {"threads": 256})},
@@ -488,6 +489,14 @@ def run_native(args):
                 "d2h_bytes_per_step": rounds * n_items * 96},
         "clocks": clk,
     }
+    if args.order >= 4:
+        # Table 1's columns per gauge-invariant class (k, m, n): value, N_diag
+        # (mirror-reduced graphs), sum |a_j|, max |a_j|
+        from paper_1905_08007_b300.classes import class_table
+        line["set_total"]["classes"] = class_table(graphs, results, mw)
+        line["set_total"]["max_abs_a_j"] = max(abs(w * r.value) for w, r in zip(mw, results))
+        if args.order == 5:
+            line["set_total"]["table1_max_abs_a_j"] = 85.8
     if ws == 1 and args.compare and args.order in (2, 3, 4):
         line["plain_per_graph"] = compare_plain(diags, graphs, ctx, S, args.seed, tmax / args.steps, sigma, q)
     if ws == 1 and args.order != 2 and args.order <= 4:
@@ -515,6 +524,8 @@ def main(argv=None):
                          "double-double: at four loops every accepted point was measured within 0.55 x the "
                          "threshold of its double-double value (2.4e-7 at 1e-6), far below any run's "
                          "statistical error")
+    ap.add_argument("--rng", default="philox", choices=["philox", "mrg32k3a"],
+                    help="generator of the sample points (Sec. 3: Calc 2 used Philox4x32-10, Calc 1 MRG32k3a)")
     ap.add_argument("--graph-stride", type=int, default=1,
                     help="every k-th graph of the set only (a small case for ncu captures)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",

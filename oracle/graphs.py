@@ -191,7 +191,7 @@ def i_closure(g: Graph, s) -> frozenset:
     return frozenset(out)
 
 
-def deg_default(g: Graph, s, c_div: float = 0.5, d_min: float = 0.05) -> float:
+def deg_default(g: Graph, s, c_div: float = 0.5, d_min: float = 0.05, omega_factor: float = 0.5) -> float:
     """Deg(s) reading: half of -omega of the I-closure when that is positive,
     else the constant c_div for sets whose closure is UV divergent, floored
     at d_min.  omega counts powers of momentum; in the Feynman parameters of
@@ -199,13 +199,15 @@ def deg_default(g: Graph, s, c_div: float = 0.5, d_min: float = 0.05) -> float:
     inverse square of its line's momentum), which is the exponent the bound
     of Eq. (1) needs, and it makes Deg fractional (1/2 for one electron
     line), as the text after Eq. (1) says Deg can be.  Parity unpinned as to
-    the value: any positive Deg gives an unbiased estimator."""
+    the value: any positive Deg gives an unbiased estimator.  omega_factor
+    = 1 gives the earlier reading Deg = -omega (too steep by two, kept to
+    reproduce points stored with it)."""
     w = -omega(g, i_closure(g, s))
-    d = 0.5 * float(w) if w > 0 else c_div
+    d = omega_factor * float(w) if w > 0 else c_div
     return max(d, d_min)
 
 
-def deg_table(g: Graph, c_div: float = 0.5, d_min: float = 0.05):
+def deg_table(g: Graph, c_div: float = 0.5, d_min: float = 0.05, omega_factor: float = 0.5):
     """Deg over all subsets of lines as a list indexed by bitmask; entries
     for the empty and the full set are unused and set to 0."""
     N = g.n_lines
@@ -213,7 +215,7 @@ def deg_table(g: Graph, c_div: float = 0.5, d_min: float = 0.05):
     tab = [0.0] * (1 << N)
     for mask in range(1, full):
         s = [l for l in range(N) if mask >> l & 1]
-        tab[mask] = deg_default(g, s, c_div, d_min)
+        tab[mask] = deg_default(g, s, c_div, d_min, omega_factor)
     return tab
 
 

@@ -52,6 +52,15 @@ struct BatchParams {
   unsigned int *next_tile;          // tile counter of the bytecode dd pass, zeroed every round
   uint32_t rng, mrg_bits;           // generator (0 Philox, 1 MRG32k3a), sample index bits
   const uint32_t *mrg_jump;         // MRG32k3a jump table
+  // compacted double-double pass of bytecode batches: flat numbering of the
+  // flagged points (item it's list starts at dd_start[it]), tiles that never
+  // straddle two graphs, per-point results folded per item afterwards
+  uint32_t *dd_start;               // [n_items + 1]
+  uint4 *dd_tab;                    // [dd_tab_cap] (item holding the tile's first point, flat begin, flat end, segment end item)
+  unsigned int *dd_ntiles;          // tiles of this round (written by the plan kernel)
+  uint32_t dd_tab_cap, dd_tile;     // tile table capacity, points per tile (the dd kernel's block size)
+  double *dd_w;                     // [n_items][list_cap] w of an accepted point
+  double *dd_u;                     // [n_items][list_cap] -1 for an accepted point, else |w| (0 if not finite)
 };
 
 __device__ __forceinline__ KParams batch_kparams(const BatchParams &B, const BatchDiag &D) {

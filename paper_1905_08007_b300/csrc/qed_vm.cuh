@@ -629,49 +629,69 @@ __global__ void __launch_bounds__(256) k_batch_vm_fp64(BatchParams B) {
   }
 }
 
-// The double-double pass over the items' flagged lists, in tiles of one
-// point per thread: tile t covers entries [k * blockDim, (k + 1) * blockDim)
-// of item t / dd_tiles's list (k = t % dd_tiles), blocks take tiles from a
-// device counter, and every tile writes its own partial (zeros when the
-// list is shorter), which the host folds per item in tile order.
+// The double-double pass of a bytecode batch, in three kernels:
+//  1. k_batch_vm_dd_plan numbers the flagged points of the round in item
+//     order (dd_start) and cuts each graph's points -- its items are
+//     consecutive in the queue -- into tiles of dd_tile points, so that a
+//     tile holds one program and every tile but a graph's last is full (the
+//     double-double frame leaves room for one block per SM, and an item's
+//     list alone fills a fraction of a block);
+//  2. k_batch_vm_dd: blocks take tiles from a device counter, one point per
+//     thread, and write each point's result to its list slot;
+//  3. k_batch_vm_dd_fold: one warp per item folds its slots in list order
+//     into the item's double-double partial, so the result does not depend
+//     on which block ran which tile.
+__global__ void k_batch_vm_dd_plan(BatchParams B) {
+  if (threadIdx.x != 0) return;
+  unsigned int t = 0;
+  uint32_t flat = 0;
+  unsigned int it = 0;
+  while (it < B.n_items) {
+    const uint32_t g = B.items[it].diag;
+    const unsigned int seg0 = it;
+    const uint32_t f0 = flat;
+    for (; it < B.n_items && B.items[it].diag == g; ++it) {
+      B.dd_start[it] = flat;
+      const unsigned long long c = B.cnt[2 * size_t(it)];
+      flat += uint32_t(c < B.list_cap ? c : B.list_cap);
+    }
+    unsigned int cur = seg0;                       // item holding flat point f
+    for (uint32_t f = f0; f < flat && t < B.dd_tab_cap; f += B.dd_tile) {
+      while (cur + 1 < it && B.dd_start[cur + 1] <= f) ++cur;
+      const uint32_t e = flat - f < B.dd_tile ? flat : f + B.dd_tile;
+      B.dd_tab[t++] = make_uint4(cur, f, e, it);
+    }
+  }
+  B.dd_start[B.n_items] = flat;
+  *B.dd_ntiles = t;
+}
+
 template <int N>
 __global__ void __launch_bounds__(256) k_batch_vm_dd(BatchParams B) {
   extern __shared__ __align__(16) unsigned char vsm[];
   __shared__ unsigned int s_tile;
-  const unsigned int n_tiles = B.n_items * B.dd_tiles;
+  const unsigned int n_tiles = *B.dd_ntiles;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(B.next_tile, 1u);
     __syncthreads();
     const unsigned int t = s_tile;
     __syncthreads();
     if (t >= n_tiles) break;
-    const unsigned int it = t / B.dd_tiles, k = t % B.dd_tiles;
-    const unsigned long long nflag = B.cnt[2 * size_t(it)];
-    const uint64_t total = nflag < B.list_cap ? nflag : B.list_cap;
-    const uint64_t start = uint64_t(k) * blockDim.x;
-    if (start >= total) {
-      if (threadIdx.x == 0) {
-        double *p = B.part_dd + QED_PART * size_t(t);
-        p[0] = p[1] = p[2] = p[3] = p[4] = 0.0;
-        B.cnt_dd[2 * size_t(t)] = 0;
-        B.cnt_dd[2 * size_t(t) + 1] = 0;
-      }
-      continue;
-    }
-    const BatchItem I = B.items[it];
-    const BatchDiag &D = B.diags[I.diag];
+    const uint4 T = B.dd_tab[t];
+    const BatchDiag &D = B.diags[B.items[T.x].diag];
     const KParams K = batch_kparams(B, D);
     const VmCode C = {D.vins, D.vkon, D.vnk, D.vnr};
     VmFrame<dd, 1> fr;
     fr.setup(C, vsm);
-    KSum sw, sw2;
-    unsigned long long nunst = 0;
-    double uw = 0.0;
-    const uint64_t i = start + threadIdx.x;
-    if (i < total) {
-      const uint32_t off = B.lists[size_t(it) * B.list_cap + i];
+    const uint32_t p = T.y + threadIdx.x;
+    if (p < T.z) {
+      unsigned int it = T.x;
+      while (it + 1 < T.w && B.dd_start[it + 1] <= p) ++it;
+      const uint32_t pos = p - B.dd_start[it];
+      const size_t slot = size_t(it) * B.list_cap + pos;
+      const uint32_t off = B.lists[slot];
       double z[N];
-      const double lp = draw_point<N>(I.begin + off, K, K.F, K.G, K.invdeg, z);
+      const double lp = draw_point<N>(B.items[it].begin + off, K, K.F, K.G, K.invdeg, z);
       dd zd[1][N], f[1];
       double ab[1];
 #pragma unroll
@@ -679,15 +699,39 @@ __global__ void __launch_bounds__(256) k_batch_vm_dd(BatchParams B) {
       fr.template eval<N>(C, zd, f, ab);
       const double w = (f[0].hi + f[0].lo) * exp(-lp);
       if (!isfinite(w) || !(rel_err_estimate(f[0].hi, ab[0], 1.2325951644078309e-32) <= K.thresh)) {
-        ++nunst;
-        if (isfinite(w)) uw += fabs(w);
+        B.dd_w[slot] = 0.0;
+        B.dd_u[slot] = isfinite(w) ? fabs(w) : 0.0;
       } else {
-        sw.add(w);
-        sw2.add(w * w);
+        B.dd_w[slot] = w;
+        B.dd_u[slot] = -1.0;
       }
     }
-    block_reduce_store(sw, sw2, 0ull, nunst, B.part_dd, B.cnt_dd, t, uw);
+    __syncthreads();     // the frame is set up again for the next tile
   }
+}
+
+// One 32-thread block per item.
+__global__ void __launch_bounds__(32) k_batch_vm_dd_fold(BatchParams B) {
+  const unsigned int it = blockIdx.x;
+  if (it >= B.n_items) return;
+  const unsigned long long c = B.cnt[2 * size_t(it)];
+  const uint32_t total = uint32_t(c < B.list_cap ? c : B.list_cap);
+  KSum sw, sw2;
+  unsigned long long nunst = 0;
+  double uw = 0.0;
+  for (uint32_t pos = threadIdx.x; pos < total; pos += 32) {
+    const size_t slot = size_t(it) * B.list_cap + pos;
+    const double u = B.dd_u[slot];
+    if (u < 0.0) {
+      const double w = B.dd_w[slot];
+      sw.add(w);
+      sw2.add(w * w);
+    } else {
+      ++nunst;
+      uw += u;
+    }
+  }
+  block_reduce_store(sw, sw2, 0ull, nunst, B.part_dd, B.cnt_dd, it, uw);
 }
 
 // ---------------------------------------------------------------------------

@@ -872,11 +872,12 @@ extern "C" int qed_eval_points(qed_diag *d, const double *z_dev, uint64_t n, int
 }
 
 extern "C" int qed_eval_interval(qed_diag *d, const double *z_dev, uint64_t n, double *lo_dev, double *hi_dev) {
-  if (!d || !z_dev || !lo_dev || !hi_dev) return set_err(QED_EINVAL, "bad argument");
+  if (!d) return set_err(QED_EINVAL, "diag is NULL");
   if (d->vm < 0)
     return set_err(QED_EINVAL, "interval arithmetic runs on bytecode programs: load the graph on a "
                                "QED_CTX_PREFER_PROGRAMS context");
   if (n == 0) return QED_OK;
+  if (!z_dev || !lo_dev || !hi_dev) return set_err(QED_EINVAL, "NULL buffer");
   qed_ctx *c = d->ctx;
   CUDA_TRY(cudaSetDevice(c->device));
   VmLaunch L;
@@ -1013,9 +1014,12 @@ struct BatchPlan {
   cudaStream_t user_stream = 0;
   int rng = 0;
   uint32_t mrg_bits = 0;
+  bool vm = false;                  // bytecode batch: compacted double-double pass
   // resources: dev = {graph descriptors, items, next-item counters, FP64
-  // partials, FP64 counts, dd partials, dd counts, flagged lists}
-  void *dev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // partials, FP64 counts, dd partials, dd counts, flagged lists, and for
+  // bytecode batches the dd plan: flat starts, tile table, tile count,
+  // per-point w, per-point unstable |w|}
+  void *dev[13] = {nullptr};
   void *h_items = nullptr, *h_out = nullptr;
   double *o_part = nullptr, *o_pdd = nullptr;
   unsigned long long *o_cnt = nullptr, *o_cdd = nullptr;
@@ -1030,13 +1034,13 @@ struct BatchPlan {
            list_cap == o.list_cap && dd_tiles == o.dd_tiles && kern1 == o.kern1 && kern2 == o.kern2 &&
            grid1 == o.grid1 && grid2 == o.grid2 && thr1 == o.thr1 && thr2 == o.thr2 && smem == o.smem &&
            smem2 == o.smem2 && use_graph == o.use_graph && user_stream == o.user_stream && rng == o.rng &&
-           mrg_bits == o.mrg_bits;
+           mrg_bits == o.mrg_bits && vm == o.vm;
   }
   BatchPlan() = default;
   BatchPlan(const BatchPlan &key) : diags(key.diags), seed(key.seed), thresh(key.thresh), n_items(key.n_items),
       list_cap(key.list_cap), dd_tiles(key.dd_tiles), kern1(key.kern1), kern2(key.kern2), grid1(key.grid1),
       grid2(key.grid2), thr1(key.thr1), thr2(key.thr2), smem(key.smem), smem2(key.smem2),
-      use_graph(key.use_graph), user_stream(key.user_stream), rng(key.rng), mrg_bits(key.mrg_bits) {}
+      use_graph(key.use_graph), user_stream(key.user_stream), rng(key.rng), mrg_bits(key.mrg_bits), vm(key.vm) {}
   BatchPlan &operator=(const BatchPlan &) = delete;
   ~BatchPlan() {
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -1057,7 +1061,9 @@ struct BatchPlan {
     CUDA_TRY(cudaEventRecordWithFlags(c->evk0, s, evflags));
     CUDA_TRY(cudaLaunchKernel(kern1, dim3(grid1), dim3(thr1), args, smem, s));
     CUDA_TRY(cudaEventRecordWithFlags(c->evk1, s, evflags));
+    if (vm) CUDA_TRY(cudaLaunchKernel((const void *)k_batch_vm_dd_plan, dim3(1), dim3(32), args, 0, s));
     CUDA_TRY(cudaLaunchKernel(kern2, dim3(grid2), dim3(thr2), args, smem2, s));
+    if (vm) CUDA_TRY(cudaLaunchKernel((const void *)k_batch_vm_dd_fold, dim3(n_items), dim3(32), args, 0, s));
     CUDA_TRY(cudaEventRecordWithFlags(c->evk2, s, evflags));
     CUDA_TRY(cudaMemcpyAsync(o_part, dev[3], sizeof(double) * QED_PART * n_items, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(o_pdd, dev[5], sizeof(double) * QED_PART * n_dd, cudaMemcpyDeviceToHost, s));
@@ -1076,6 +1082,16 @@ struct BatchPlan {
     CUDA_TRY(cudaMalloc(&dev[5], sizeof(double) * QED_PART * n_dd));
     CUDA_TRY(cudaMalloc(&dev[6], sizeof(unsigned long long) * 2 * n_dd));
     CUDA_TRY(cudaMalloc(&dev[7], sizeof(uint32_t) * size_t(list_cap) * n_items));
+    uint32_t tab_cap = 0;
+    if (vm) {
+      // tiles: at most (all points) / tile + one partial tile per graph
+      tab_cap = uint32_t((size_t(n_items) * list_cap + thr2 - 1) / size_t(thr2) + size_t(k) + 1);
+      CUDA_TRY(cudaMalloc(&dev[8], sizeof(uint32_t) * (size_t(n_items) + 1)));
+      CUDA_TRY(cudaMalloc(&dev[9], sizeof(uint4) * size_t(tab_cap)));
+      CUDA_TRY(cudaMalloc(&dev[10], sizeof(unsigned int)));
+      CUDA_TRY(cudaMalloc(&dev[11], sizeof(double) * size_t(list_cap) * n_items));
+      CUDA_TRY(cudaMalloc(&dev[12], sizeof(double) * size_t(list_cap) * n_items));
+    }
     const size_t out_bytes = n_items * (QED_PART * sizeof(double) + 2 * sizeof(unsigned long long)) +
                              n_dd * (QED_PART * sizeof(double) + 2 * sizeof(unsigned long long));
     CUDA_TRY(cudaMallocHost(&h_items, sizeof(BatchItem) * n_items));
@@ -1091,6 +1107,9 @@ struct BatchPlan {
     B.part_dd = (double *)dev[5]; B.cnt_dd = (unsigned long long *)dev[6];
     B.dd_tiles = dd_tiles; B.next_tile = (unsigned int *)dev[2] + 1;
     B.rng = uint32_t(rng); B.mrg_bits = mrg_bits; B.mrg_jump = c->mrg_jump;
+    B.dd_start = (uint32_t *)dev[8]; B.dd_tab = (uint4 *)dev[9]; B.dd_ntiles = (unsigned int *)dev[10];
+    B.dd_tab_cap = tab_cap; B.dd_tile = uint32_t(thr2);
+    B.dd_w = (double *)dev[11]; B.dd_u = (double *)dev[12];
     st = user_stream;
     if (use_graph) {
       if (st == 0) { CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own_stream = true; }
@@ -1161,13 +1180,14 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
     if (rc) return rc;
     smem = L1.smem; smem2 = L2.smem; thr1 = L1.threads; thr2 = L2.threads;
   }
-  // bytecode batches: the dd pass runs in tiles of one point per thread
-  const uint32_t dd_tiles = vmb ? uint32_t((chunk + uint64_t(thr2) - 1) / uint64_t(thr2)) : 1u;
-  const size_t n_dd = size_t(n_items) * dd_tiles;
+  // one double-double partial per item (bytecode batches: folded per item
+  // from the compacted pass's per-point results)
+  const uint32_t dd_tiles = 1u;
+  const size_t n_dd = size_t(n_items);
   int occ = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern1, thr1, smem));
   const int grid1 = std::max(1, occ) * c->sms;
-  const int grid2 = vmb ? int(std::min<size_t>(n_dd, size_t(L2.blocks))) : std::min<int>(int(n_items), 4 * c->sms);
+  const int grid2 = vmb ? L2.blocks : std::min<int>(int(n_items), 4 * c->sms);
   // the set-up (buffers, pinned memory, the captured round) is kept on the
   // context and reused while the batch's shape is the same
   BatchPlan key;
@@ -1176,6 +1196,7 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
   key.kern1 = kern1; key.kern2 = kern2; key.grid1 = grid1; key.grid2 = grid2; key.thr1 = thr1; key.thr2 = thr2;
   key.smem = smem; key.smem2 = smem2; key.use_graph = o.use_graph >= 0; key.user_stream = c->stream;
   key.rng = c->rng;
+  key.vm = vmb;
   if (c->rng == QED_RNG_MRG32K3A) {
     // every sample index of the call is below counter_base + rounds x items
     // x chunk; rounded up to a multiple of 8 bits so that the captured round
@@ -1261,7 +1282,7 @@ extern "C" int qed_integrate_batch(qed_ctx *c, qed_diag *const *d, int k, uint64
       }
     if (gexec) { CUDA_TRY(cudaGraphLaunch(gexec, st)); }
     else { int rc = PL.enqueue_round(c, st, false); if (rc) return rc; }
-    launches += 2;
+    launches += vmb ? 4 : 2;
     CUDA_TRY(cudaStreamSynchronize(st));
     {
       float kms = 0.f;

@@ -1,9 +1,16 @@
 """Writes four_loop_points.txt: oracle values of the four-loop integrands at
 the points that Eq. (1)'s sampler draws from given Philox counters (seed 0,
-stream id = the graph's index in the full enumeration, default Deg table).
+stream id = the graph's index in the full enumeration) with the Deg table
+Deg(s) = -omega(I-closure(s)), else 0.5, floored at 0.05 (deg_table with
+omega_factor 1: the file was written before Deg took half of -omega; any
+positive table serves parity, and the tests give the library the same one).
 Calls only oracle/.
 
-    python tests/golden/make_four_loop.py [--procs 6]
+    python tests/golden/make_four_loop.py [--procs 6] [--graphs G ...] [--counters C ...]
+
+With --graphs / --counters only those rows are computed and they replace
+the rows of the same (graph, counter) in the existing file (the others are
+kept).
 
 Graphs: every mirror-reduced four-loop graph (269; Sec. 3 counts the
 mirror-reduced set), each at the counters in COUNTERS.  The oracle needs a few
@@ -42,7 +49,7 @@ def row(job):
     from oracle.philox import uniforms
     g = enumerate_graphs(4)[gi]
     N = g.n_lines
-    deg = deg_table(g)
+    deg = deg_table(g, omega_factor=1.0)
     u = uniforms(np.array([c], dtype=np.uint64), gi, 0, 2 * (N - 1))
     x, lp, _ = sample_points(u, deg, f_table(deg, N), N)
     f = Integrand(g)(x, dtype=np.longdouble)
@@ -53,14 +60,24 @@ def row(job):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--procs", type=int, default=6)
+    ap.add_argument("--graphs", type=int, nargs="*", default=None)
+    ap.add_argument("--counters", type=int, nargs="*", default=None)
     a = ap.parse_args()
+    gis = a.graphs if a.graphs else graphs()
+    counters = a.counters if a.counters else COUNTERS
+    keep = {}
+    if (a.graphs or a.counters) and OUT.exists():
+        for ln in OUT.read_text().splitlines():
+            p = ln.split()
+            if len(p) == 16 and not ln.startswith("#"):
+                keep[(int(p[0]), int(p[1]))] = ln
     done = {}
     if PARTIAL.exists():
         for ln in PARTIAL.read_text().splitlines():
             p = ln.split()
             if len(p) == 16:
                 done[(int(p[0]), int(p[1]))] = ln
-    jobs = [(gi, c) for gi in graphs() for c in COUNTERS if (gi, c) not in done]
+    jobs = [(gi, c) for gi in gis for c in counters if (gi, c) not in done]
     ctx = mp.get_context("spawn")
     with ctx.Pool(a.procs) as pool, open(PARTIAL, "a") as fh:
         for ln in pool.imap_unordered(row, jobs):
@@ -68,9 +85,12 @@ def main():
             fh.flush()
             p = ln.split()
             done[(int(p[0]), int(p[1]))] = ln
+    keep.update(done)
+    done = keep
     keys = sorted(done)
     with open(OUT, "w") as fh:
         fh.write("# four-loop integrand at Eq. (1) points (oracle, long double); written by make_four_loop.py\n")
+        fh.write("# Deg table: -omega(I-closure) (oracle deg_table with omega_factor 1), c_div 0.5, d_min 0.05\n")
         fh.write("# graph counter logp z0..z11 f\n")
         for k in keys:
             fh.write(done[k] + "\n")

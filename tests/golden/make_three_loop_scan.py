@@ -17,9 +17,11 @@ a fixed Dirichlet(1, ..., 1) generator (numpy seed 60 + graph index).
     python tests/golden/make_three_loop_scan.py [--jobs 8]
 
 Runs the oracle in float64 over all 511 - 1 proper subsets of the 9 lines of
-the 28 mirror-reduced graphs (about 57000 integrand evaluations; an hour or
-so on 8 cores).  Line format: graph index (full enumeration), subset
-bitmask, delta at base point 0, delta at base point 1.
+the 28 mirror-reduced graphs (about 57000 integrand evaluations, in batches
+of 128 points to bound the memory of the vectorised oracle; an hour or so
+on 8 cores).  Finished graphs are appended to three_loop_limit_scan.partial
+and a rerun resumes from it.  Line format: graph index (full enumeration),
+subset bitmask, delta at base point 0, delta at base point 1.
 """
 from __future__ import annotations
 
@@ -36,6 +38,8 @@ sys.path.insert(0, str(HERE.parents[1]))
 
 EPS = (1e-3, 1e-5)
 N = 9
+BATCH = 128
+PARTIAL = HERE / "three_loop_limit_scan.partial"
 
 
 def reduced_indices():
@@ -69,7 +73,8 @@ def scan_graph(gi, masks=None):
                 if m >> l & 1:
                     z[:, l] *= e
             pts.append(z)
-    vals = np.abs(f(np.concatenate(pts, axis=0)))
+    allz = np.concatenate(pts, axis=0)
+    vals = np.concatenate([np.abs(f(allz[i:i + BATCH])) for i in range(0, len(allz), BATCH)])
     out = []
     k = 0
     for m in masks:
@@ -82,22 +87,37 @@ def scan_graph(gi, masks=None):
     return out
 
 
+def _job(gi):
+    return gi, scan_graph(gi)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--jobs", type=int, default=8)
     ap.add_argument("--out", default=str(HERE / "three_loop_limit_scan.txt"))
     a = ap.parse_args(argv)
     gis = reduced_indices()
+    done = {}
+    if PARTIAL.exists():
+        for ln in PARTIAL.read_text().splitlines():
+            gi, m, d0, d1 = ln.split()
+            done.setdefault(int(gi), []).append(ln)
+    todo = [g for g in gis if len(done.get(g, [])) != (1 << N) - 2]
     with mp.get_context("spawn").Pool(a.jobs) as pool:
-        res = pool.map(scan_graph, gis, chunksize=1)
+        for gi, rows in pool.imap_unordered(_job, todo):
+            text = "".join(f"{gi} {m} {d0:.6f} {d1:.6f}\n" for m, d0, d1 in rows)
+            with open(PARTIAL, "a") as fh:
+                fh.write(text)
+            done[gi] = text.splitlines()
+            print(f"graph {gi} done ({len(done)}/{len(gis)})", flush=True)
     lines = ["# local exponent delta of |f| eps^|S| under z_S -> eps z_S between eps = 1e-3 and 1e-5,",
              "# two base points per graph (Dirichlet(1,...,1), numpy seed 60 + graph index); written by",
              "# tests/golden/make_three_loop_scan.py from the oracle (float64)",
              "# graph_index subset_mask delta_point0 delta_point1"]
-    for gi, rows in zip(gis, res):
-        for m, d0, d1 in rows:
-            lines.append(f"{gi} {m} {d0:.6f} {d1:.6f}")
+    for gi in gis:
+        lines.extend(sorted(done[gi], key=lambda ln: int(ln.split()[1])))
     Path(a.out).write_text("\n".join(lines) + "\n")
+    PARTIAL.unlink()
     print(f"wrote {a.out}: {len(gis)} graphs")
 
 

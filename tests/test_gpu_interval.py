@@ -55,16 +55,16 @@ def _check_encloses_dd(d, z):
     return lo, hi, fdd, fin
 
 
-@pytest.mark.parametrize("gi", range(6))
+@pytest.mark.parametrize("gi", range(4))
 def test_two_loop_interval_encloses_dd_and_the_oracle(ctx, gi):
-    g = q.enumerate_graphs(2)[gi]
+    # the programs exist for one graph of each mirror pair
+    g = q.enumerate_graphs(2, reduced=True)[gi]
     d = ctx.load(g)
-    assert d.integrand_id >= 0
     z, f, lp, fl = d.dump_points(0, 700, seed=5)
     lo, hi, fdd, fin = _check_encloses_dd(d, z)
     # the oracle in 34-digit arithmetic on a subsample
     import mpmath
-    og = o_enum(2)[gi]
+    og = next(x for x in o_enum(2) if (tuple(x.pairs), x.e) == (tuple(g.pairs), g.e))
     zz = z.cpu().numpy()
     idx = [i for i in range(0, 700, 35) if fin[i]]
     with mpmath.workdps(34):
@@ -118,9 +118,9 @@ def test_degenerate_inputs(ctx):
         dc.integrate(1000)
 
 
-@pytest.mark.parametrize("gi", [1, 4])
+@pytest.mark.parametrize("gi", [1, 3])
 def test_interval_rule_integration_matches_estimate_rule(gi):
-    g = q.enumerate_graphs(2)[gi]
+    g = q.enumerate_graphs(2, reduced=True)[gi]
     res = {}
     for rule in ("estimate", "interval"):
         c = q.Context(0, threshold=1e-9, prefer_programs=True, flag_rule=rule)

@@ -145,7 +145,7 @@ def test_four_loop_points_match_oracle(ctx4):
     if not GOLDEN4.exists():
         pytest.skip("four_loop_points.txt not written")
     from tests.test_programs import interpret, read_programs, _name
-    from oracle.graphs import enumerate_graphs as o_enum
+    from oracle.graphs import deg_table, enumerate_graphs as o_enum
     progs = read_programs(ROOT / "paper_1905_08007_b300" / "csrc" / "_gen" / "vm_n4.bin.z")
     strict = q.Context(0, threshold=1e-12)
     gs = q.enumerate_graphs(4)
@@ -153,7 +153,9 @@ def test_four_loop_points_match_oracle(ctx4):
     golden = _golden4()
     n_fp64 = n_dd = 0
     for gi, rs in golden.items():
-        d = strict.load(gs[gi])
+        # the stored points were drawn with Deg = -omega(I-closure): the
+        # library gets the same table
+        d = strict.load(gs[gi], deg=deg_table(ogs[gi], omega_factor=1.0))
         assert d.n_lines == 12
         zs, fs, lps, fls = [], [], [], []
         for r in rs:
