@@ -112,7 +112,13 @@ def test_programs_well_formed(n):
         red = [every[i] for i in read()]
     else:
         red = [g for g in o_enum(n) if tuple(g.key()) <= tuple(g.mirror().key())]
-    assert sorted(progs) == sorted(_name(g) for g in red)
+    if n == 5:
+        # five-loop programs are generated graph by graph on request: a
+        # file may hold part of the workload, in its order
+        names = [_name(g) for g in red]
+        assert progs and set(progs) <= set(names)
+    else:
+        assert sorted(progs) == sorted(_name(g) for g in red)
     for name, p in progs.items():
         assert p["n_lines"] == 3 * n and p["n_lines"] <= p["n_regs"] <= 1023 and len(p["kon"]) <= 4096
         ins = p["ins"]
