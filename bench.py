@@ -49,12 +49,13 @@ SIGMA_TARGET = 1e-5
 # time-to-sigma target per loop order (four loops: sigma_total = 5e-3)
 SIGMA_TARGETS = {1: 1e-5, 2: 1e-5, 3: 1e-4, 4: 5e-3, 5: 0.1}
 # samples per graph per step: 6e8 per step on the two-loop set, 1e9 on the
-# three-loop set, 1.76e7 on the 269 four-loop graphs
-DEFAULT_SAMPLES = {1: 1e8, 2: 1e8, 3: 2e7, 4: 2 ** 16, 5: 2 ** 12}
+# three-loop set, 8.8e6 on the 269 four-loop graphs (about 5 s of device
+# time), 2^16 per graph of the five-loop workload
+DEFAULT_SAMPLES = {1: 1e8, 2: 1e8, 3: 2e7, 4: 2 ** 15, 5: 2 ** 16}
 # work-item size of the batched kernel per order (a four-loop sample is ~1e5
 # FP64 operations, a five-loop one ~1e6): at four loops 2048 samples give
 # about 15 items per persistent block and round, so the blocks finish together
-CHUNK = {1: 1 << 18, 2: 1 << 18, 3: 1 << 18, 4: 1 << 11, 5: 1 << 11}
+CHUNK = {1: 1 << 18, 2: 1 << 18, 3: 1 << 18, 4: 1 << 11, 5: 1 << 8}
 CLOSED_FORM = {1: 0.5, 2: TWO_LOOP_TARGET}
 
 
@@ -356,7 +357,10 @@ def run_native(args):
         if ts:
             tune(d, steps=ts, n=tn, lr=0.08, seed=args.seed + 7)
     autotuned = None
-    if args.autotune and args.order >= 4:
+    # the autotuner's short batches are a few seconds at four loops; at five
+    # loops (1e6 FP64 operations a sample, most points flagged) the default
+    # shape and items of 256 samples are used
+    if args.autotune and args.order == 4:
         from paper_1905_08007_b300.autotune import tune_batch_chunk, tune_vm
         small = max(1 << 19, 4 * len(diags) * CHUNK[args.order])
         best_vm, tab_vm = tune_vm(ctx, diags, samples=small, chunk=CHUNK[args.order])
