@@ -7,7 +7,9 @@
 // item's samples in FP64 and writes one partial per item; flagged samples go
 // to the item's own list in a fixed order (warp ballots and a block prefix
 // sum, not atomics).  Kernel 2 (k_batch_dd) re-evaluates each item's list in
-// double-double.  All partials are per item, so the host fold (items in index
+// double-double (bytecode batches: k_batch_vm_dd over full tiles of each
+// graph's flagged points, between a plan and a per-item fold kernel; see
+// qed_vm.cuh).  All partials are per item, so the host fold (items in index
 // order) is deterministic whatever block ran an item.  The host sets the
 // items of each round from the running per-graph variances (Neyman
 // allocation) and replays a captured CUDA graph.
@@ -46,9 +48,9 @@ struct BatchParams {
   unsigned long long *cnt;          // [n_items][2]  flagged, (unused)
   uint32_t *lists;                  // [n_items][list_cap] flagged offsets
   uint32_t list_cap;
-  double *part_dd;                  // [n_items * dd_tiles][QED_PART]  double-double moments
-  unsigned long long *cnt_dd;       // [n_items * dd_tiles][2]  (unused), unstable
-  uint32_t dd_tiles;                // double-double tiles per item (1: one block per item)
+  double *part_dd;                  // [n_items][QED_PART]  double-double moments (one partial per item)
+  unsigned long long *cnt_dd;       // [n_items][2]  (unused), unstable
+  uint32_t dd_tiles;                // double-double partials per item (1)
   unsigned int *next_tile;          // tile counter of the bytecode dd pass, zeroed every round
   uint32_t rng, mrg_bits;           // generator (0 Philox, 1 MRG32k3a), sample index bits
   const uint32_t *mrg_jump;         // MRG32k3a jump table
