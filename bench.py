@@ -48,14 +48,14 @@ TWO_LOOP_TARGET = (197 / 144 + math.pi ** 2 / 12 - math.pi ** 2 * math.log(2) / 
 SIGMA_TARGET = 1e-5
 # time-to-sigma target per loop order (four loops: sigma_total = 5e-3)
 SIGMA_TARGETS = {1: 1e-5, 2: 1e-5, 3: 1e-4, 4: 5e-3, 5: 0.1}
-# samples per graph per step: 6e8 per step on the two-loop set, 1e9 on the
-# three-loop set, 8.8e6 on the 269 four-loop graphs (about 5 s of device
-# time), 2^16 per graph of the five-loop workload
-DEFAULT_SAMPLES = {1: 1e8, 2: 1e8, 3: 2e7, 4: 2 ** 15, 5: 2 ** 16}
+# samples per graph per step: 6e8 per step on the two-loop set, 1.2e8 on the
+# 28 mirror-reduced three-loop graphs, 8.8e6 on the 269 four-loop graphs
+# (about 5 s of device time), 2^16 per graph of the five-loop workload
+DEFAULT_SAMPLES = {1: 1e8, 2: 1e8, 3: 2 ** 22, 4: 2 ** 15, 5: 2 ** 16}
 # work-item size of the batched kernel per order (a four-loop sample is ~1e5
 # FP64 operations, a five-loop one ~1e6): at four loops 2048 samples give
 # about 15 items per persistent block and round, so the blocks finish together
-CHUNK = {1: 1 << 18, 2: 1 << 18, 3: 1 << 18, 4: 1 << 11, 5: 1 << 8}
+CHUNK = {1: 1 << 18, 2: 1 << 18, 3: 1 << 14, 4: 1 << 11, 5: 1 << 8}
 CLOSED_FORM = {1: 0.5, 2: TWO_LOOP_TARGET}
 
 
@@ -134,15 +134,20 @@ def mirror_weights(graphs):
 
 
 def graph_set(q, order):
-    """The benchmarked set: every graph up to three loops (mirror pairs both
-    present), one per mirror pair at four loops (bytecode integrands), the
-    64-graph five-loop workload (five_loop_subset.txt) at five."""
+    """The benchmarked set: every graph at one and two loops (mirror pairs
+    both present, compiled integrands), one per mirror pair at three and
+    four loops (bytecode integrands, mirror weights), the 64-graph five-loop
+    workload (five_loop_subset.txt) at five.  At three loops the compiled
+    integrands' double-double versions spill registers and ran the flagged
+    points at 0.004 of the FP64 peak (59 of 63 s of a 1e8-sample step with 2 %
+    flagged), while the interpreter's compacted double-double pass runs
+    them at about 0.4."""
     if order == 5:
         from paper_1905_08007_b300.five_loop_subset import read
         every = q.enumerate_graphs(5)
         gs = [every[i] for i in read()]
         return gs, [1.0] * len(gs)
-    if order == 4:
+    if order in (3, 4):
         gs = q.enumerate_graphs(order, reduced=True)
         return gs, mirror_weights(gs)
     gs = q.enumerate_graphs(order)
@@ -210,14 +215,13 @@ def cpu_baseline(order=4, seed=0):
             "note": "numpy FP64 oracle as it stands; a reported baseline, not a target"}
 
 
-def compare_plain(diags, graphs, ctx, S, seed, t_step, sigma_step, q):
+def compare_plain(diags, graphs, mw, ctx, S, seed, t_step, sigma_step, q):
     """The plain per-graph path on the same budget: untuned Eq. (1) densities
     (the Deg rule), equal samples per graph, one launch per graph; time to
     the target sigma against the batched, calibrated, tuned step."""
     plain = [ctx.load(g) for g in graphs]
     res = [d.integrate(S, seed=seed + 1, begin=1 << 41) for d in plain]
     t = sum(r.seconds for r in res)
-    mw = mirror_weights(graphs) if graphs[0].n >= 4 else [1.0] * len(graphs)
     sig = math.sqrt(sum(w * w * r.variance for w, r in zip(mw, res)))
     st = SIGMA_TARGETS[graphs[0].n]
     tts_plain = t * (sig / st) ** 2
@@ -316,7 +320,8 @@ def run_native(args):
     torch.cuda.set_device(local)
     import paper_1905_08007_b300 as q
     from paper_1905_08007_b300.tune import tune
-    ctx = q.Context(local, threshold=args.threshold, rng=args.rng)
+    # three loops: the bytecode programs (see graph_set)
+    ctx = q.Context(local, threshold=args.threshold, rng=args.rng, prefer_programs=args.order == 3)
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream)
     graphs, mw = graph_set(q, args.order)
@@ -441,11 +446,11 @@ def run_native(args):
     tot = sum(w * r.value for w, r in zip(mw, results))
     sigma = math.sqrt(sum(w * w * r.variance for w, r in zip(mw, results)))
     peak = fp64_peak / 1e12
-    k64 = {"name": ("k_batch_fp64 (persistent FP64 integration kernel)" if args.order <= 3 else
+    k64 = {"name": ("k_batch_fp64 (persistent FP64 integration kernel)" if args.order <= 2 else
                     f"k_batch_vm_fp64<{3 * args.order}> (persistent FP64 interpreter kernel, bytecode integrands)"),
            "seconds": ksec, "achieved": alg / ksec / 1e12, "frac": alg / ksec / 1e12 / peak,
            "flops": alg}
-    kdd = {"name": ("k_batch_dd (double-double pass)" if args.order <= 3 else
+    kdd = {"name": ("k_batch_dd (double-double pass)" if args.order <= 2 else
                     f"k_batch_vm_dd<{3 * args.order}> (double-double interpreter pass)"),
            "seconds": dsec, "achieved": algdd / dsec / 1e12 if dsec > 0 else None,
            "frac": algdd / dsec / 1e12 / peak if dsec > 0 else None, "flops": algdd,
@@ -460,7 +465,8 @@ def run_native(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (Philox counters)",
         "config": {"workload": f"{args.order}-loop lepton-loop-free vertex set: {len(graphs)} graphs"
-                               + {4: " (one per mirror pair, bytecode integrands)",
+                               + {3: " (one per mirror pair, bytecode integrands)",
+                                  4: " (one per mirror pair, bytecode integrands)",
                                   5: " of the 64-graph workload (those with generated programs, bytecode "
                                      "integrands)"}.get(args.order, "") + ", "
                                f"{total:.0e} Philox samples per step shared by running variance, "
@@ -474,7 +480,7 @@ def run_native(args):
                    "flag_threshold": args.threshold, "deg": "calibrated" if args.calibrate else "rule",
                    "rng": {"philox": "Philox4x32-10 (Calc 2)", "mrg32k3a": "MRG32k3a (Calc 1)"}[args.rng],
                    "launch": {"items_per_round": n_items, "chunk": chunk,
-                              **({"vm_threads": ctx.vm_shape[0], "vm_points": ctx.vm_shape[1]} if args.order >= 4
+                              **({"vm_threads": ctx.vm_shape[0], "vm_points": ctx.vm_shape[1]} if args.order >= 3
                                  else {"threads": 256})},
                    "setup_seconds_calibrate_and_tune": setup_s, "autotune": autotuned},
         "set_total": {"loops": args.order, "value": tot, "sigma": sigma,
@@ -517,7 +523,7 @@ def run_native(args):
         if args.order == 5:
             line["set_total"]["table1_max_abs_a_j"] = 85.8
     if ws == 1 and args.compare and args.order in (2, 3, 4):
-        line["plain_per_graph"] = compare_plain(diags, graphs, ctx, S, args.seed, tmax / args.steps, sigma, q)
+        line["plain_per_graph"] = compare_plain(diags, graphs, mw, ctx, S, args.seed, tmax / args.steps, sigma, q)
     if ws == 1 and args.order != 2 and args.order <= 4:
         line["two_loop_total"] = two_loop_pull(q, ctx, args.seed)
     if ws == 1 and not args.no_cpu_baseline and args.order <= 4:

@@ -13,10 +13,10 @@ Steps:
 3. run the generator's bytecode back end for the program orders: it writes
    ``csrc/_gen/vm_n<n>.bin`` (one program per mirror-reduced graph; at five
    loops the 64 graphs of ``five_loop_subset.txt``, built only when asked
-   for with ``--programs 2 3 4 5``), stored zlib-compressed as
-   ``vm_n<n>.bin.z``; the library's interpreter kernels evaluate them (four
-   loops and up have no compiled integrands; the lower orders are there to
-   compare the two paths).
+   for with ``--programs 2 3 4 5``, one generator process per graph and
+   resumable), stored zlib-compressed as ``vm_n<n>.bin.z``; the library's
+   interpreter kernels evaluate them (four loops and up have no compiled
+   integrands; the lower orders are there to compare the two paths).
 """
 from __future__ import annotations
 
@@ -96,17 +96,83 @@ def build_programs(orders=DEFAULT_PROGRAM_ORDERS, force=False):
         out, stamp = GEN / f"vm_n{n}.bin.z", BUILD / f"programs_n{n}.stamp"
         if force or not (out.exists() and stamp.exists() and stamp.read_text() == keys[n]):
             todo.append(n)
+    if 5 in todo:
+        todo.remove(5)
+        build_five_loop_programs(keys[5])
     if todo:
         for n in todo:
             for old in (GEN / f"vm_n{n}.bin", GEN / f"vm_n{n}.bin.z", BUILD / f"programs_n{n}.stamp"):
                 if old.exists():
                     old.unlink()
-        subset = PKG / "five_loop_subset.txt"
-        _run([_generator(), GEN] + [f"v{n}@{subset}" if n == 5 else f"v{n}" for n in todo])
+        _run([_generator(), GEN] + [f"v{n}" for n in todo])
         for n in todo:
             compress_programs(GEN / f"vm_n{n}.bin")
             (BUILD / f"programs_n{n}.stamp").write_text(keys[n])
     return [GEN / f"vm_n{n}.bin.z" for n in orders]
+
+
+def _program_records(path):
+    """The program records of a generator file (after its 16-byte header)."""
+    import struct
+    data = Path(path).read_bytes()
+    if data[:8] != b"QEDVM004":
+        raise RuntimeError(f"{path}: not a program file")
+    (n,) = struct.unpack_from("<I", data, 8)
+    p, out = 16, []
+    for _ in range(n):
+        _, _, nins, nkon = struct.unpack_from("<4i", data, p + 64)
+        size = 64 + 16 + 8 + 8 * nins + 8 * nkon
+        out.append(data[p:p + size])
+        p += size
+    if p != len(data):
+        raise RuntimeError(f"{path}: trailing bytes")
+    return out
+
+
+def build_five_loop_programs(key, jobs=None):
+    """The 64-graph five-loop workload, one generator process per graph: a
+    graph's forest expansion is released when its process ends (one process
+    for all 64 graphs held every graph's working set and needed about 60 GB),
+    and finished graphs are kept under _build/v5/ so that a rerun resumes.
+    The programs are merged into vm_n5.bin.z in the order of
+    five_loop_subset.txt; the stamp is written only when every graph is
+    there (a partial file is still written and used)."""
+    import struct
+    subset = [int(x) for x in (PKG / "five_loop_subset.txt").read_text().split()]
+    root = BUILD / "v5"
+    root.mkdir(parents=True, exist_ok=True)
+    gen = _generator()
+    jobs = jobs or int(os.environ.get("QED_GEN_JOBS", "0")) or max(1, (os.cpu_count() or 2) // 2)
+
+    def one(gi):
+        d = root / f"g{gi}"
+        done = d / "done.stamp"
+        if done.exists() and done.read_text() == key and (d / "vm_n5.bin").exists():
+            return gi, True
+        d.mkdir(exist_ok=True)
+        (d / "list.txt").write_text(f"{gi}\n")
+        env = dict(os.environ, QED_GEN_JOBS="1")
+        r = subprocess.run([str(gen), str(d), f"v5@{d / 'list.txt'}"], env=env, capture_output=True, text=True)
+        ok = r.returncode == 0 and (d / "vm_n5.bin").exists() and len(_program_records(d / "vm_n5.bin")) == 1
+        if ok:
+            done.write_text(key)
+        else:
+            print(f"qed_gen: five-loop graph {gi} failed:\n{r.stderr[-2000:]}", flush=True)
+        return gi, ok
+
+    print(f"+ five-loop programs: {len(subset)} graphs, {jobs} generator processes", flush=True)
+    with ThreadPoolExecutor(max_workers=jobs) as ex:
+        status = dict(ex.map(one, subset))
+    blobs = [_program_records(root / f"g{gi}" / "vm_n5.bin")[0] for gi in subset if status[gi]]
+    raw = GEN / "vm_n5.bin"
+    raw.write_bytes(b"QEDVM004" + struct.pack("<2I", len(blobs), 0) + b"".join(blobs))
+    compress_programs(raw)
+    stamp = BUILD / "programs_n5.stamp"
+    if len(blobs) == len(subset):
+        stamp.write_text(key)
+    elif stamp.exists():
+        stamp.unlink()
+    print(f"+ five-loop programs: {len(blobs)} of {len(subset)} graphs", flush=True)
 
 
 def compress_programs(raw):

@@ -241,3 +241,32 @@ def test_five_loop_points(ctx4):
         rel = np.abs((f - fc.astype(float)) / fc.astype(float))
         assert np.all(rel[ok] < 1.5 * TH + 64 * 2.0 ** -64 * kappa[ok]), (gi, rel, kappa)
 
+
+
+@pytest.mark.parametrize("thresh", [1e-6, 1e-8, 1e-10])
+def test_four_loop_estimate_bounds_accepted_error(thresh):
+    """The flag rule's estimate 8 ulp kappa bounds the FP64 error of every
+    point it accepts: at Eq. (1) points of eight four-loop graphs (4096
+    each), every accepted FP64 value is within the threshold of the
+    double-double value of the same program (Sec. 3: points whose round-off
+    could matter go to a higher precision).  Prints the largest ratio of
+    true error to threshold, the margin the estimate leaves."""
+    _need_gpu()
+    c = q.Context(0, threshold=thresh)
+    gs = q.enumerate_graphs(4, reduced=True)
+    worst, n_ok, n_all = 0.0, 0, 0
+    for g in gs[::34]:
+        d = c.load(g)
+        z, f, lp, fl = d.dump_points(1 << 30, 4096, seed=4)
+        fdd = d.eval_points(z, prec=1)
+        ok = (fl == 0).cpu().numpy()
+        f, fdd = f.cpu().numpy(), fdd.cpu().numpy()
+        rel = np.abs(f[ok] - fdd[ok]) / np.abs(fdd[ok])
+        if rel.size:
+            worst = max(worst, float(rel.max()) / thresh)
+        n_ok += int(ok.sum())
+        n_all += ok.size
+        d.close()
+    assert n_ok > 0.1 * n_all
+    assert worst < 1.0, worst
+    print(f"threshold {thresh:g}: {n_ok} of {n_all} points accepted, largest error / threshold {worst:.3f}")
