@@ -546,9 +546,8 @@ def main(argv=None):
     ap.add_argument("--chunk", type=int, default=None, help="samples per work item of the batched kernel")
     ap.add_argument("--threshold", type=float, default=1e-6,
                     help="relative rounding-error threshold above which a point is re-evaluated in "
-                         "double-double: at four loops every accepted point was measured within 0.55 x the "
-                         "threshold of its double-double value (2.4e-7 at 1e-6), far below any run's "
-                         "statistical error")
+                         "double-double: at four loops every accepted point was measured within 0.21 x the "
+                         "threshold of its double-double value, far below any run's statistical error")
     ap.add_argument("--rng", default="philox", choices=["philox", "mrg32k3a"],
                     help="generator of the sample points (Sec. 3: Calc 2 used Philox4x32-10, Calc 1 MRG32k3a)")
     ap.add_argument("--graph-stride", type=int, default=1,
