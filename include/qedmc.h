@@ -16,7 +16,8 @@
  *    (vertices 0..2n-1 along the electron flow); the external photon vertex
  *    sits after the first e photon vertices.  Lines: electron lines 0..2n-1
  *    along the flow, then photons 2n..3n-1.
- *  - Random numbers: Philox4x32-10 (Sec. 3, Calc 2), counter = (sample lo32,
+ *  - Random numbers: Philox4x32-10 (Sec. 3, Calc 2; MRG32k3a, Calc 1, with
+ *    qed_ctx_set_rng), counter = (sample lo32,
  *    sample hi32, graph stream id, block), key = (seed lo32, seed hi32).
  *    Sample s uses draws 0..N-2 for the Hepp-sector walk and N-1..2N-3 for
  *    the radial variables, two draws per Philox block; draw = words (hi, lo)
@@ -217,7 +218,9 @@ int qed_eval_points(qed_diag *d, const double *z_dev, uint64_t n, int prec, doub
  * exact integrand can differ from the enclosed value by that rounding (a
  * few ulp of the sum of the absolute values of the monomials).  An interval
  * that lost every digit comes back as [-inf, inf] or with NaN ends.
- * Bytecode programs only (QED_EINVAL for a compiled integrand). */
+ * lo_dev, hi_dev: n doubles each, caller-owned device buffers (may be NULL
+ * when n = 0).  Runs on the context's stream and returns after it
+ * completed.  Bytecode programs only (QED_EINVAL for a compiled integrand). */
 int qed_eval_interval(qed_diag *d, const double *z_dev, uint64_t n, double *lo_dev, double *hi_dev);
 
 /* ---- tunable density and the adjoint of the second moment --------------- */

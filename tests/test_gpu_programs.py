@@ -270,3 +270,56 @@ def test_four_loop_estimate_bounds_accepted_error(thresh):
     assert n_ok > 0.1 * n_all
     assert worst < 1.0, worst
     print(f"threshold {thresh:g}: {n_ok} of {n_all} points accepted, largest error / threshold {worst:.3f}")
+
+
+def test_five_loop_points_match_oracle():
+    """Five loops (15 lines) against the oracle's own integrand: at the
+    oracle's stored points (tests/golden/five_loop_points.txt, long double,
+    written from oracle/ alone) the GPU's points and log p to 1e-12, its
+    accepted FP64 values (threshold 1e-12) to 1e-12, and its double-double
+    values to 1e-12 plus the long-double oracle's own rounding (16 x 2^-64 x
+    kappa of the graph's program at that point), for the stored graphs whose
+    programs were generated."""
+    _need_gpu()
+    golden5 = ROOT / "tests" / "golden" / "five_loop_points.txt"
+    path = ROOT / "paper_1905_08007_b300" / "csrc" / "_gen" / "vm_n5.bin.z"
+    if not golden5.exists() or not path.exists():
+        pytest.skip("five-loop programs or stored points missing")
+    from tests.test_programs import interpret, read_programs, _name
+    from oracle.graphs import enumerate_graphs as o_enum
+    progs = read_programs(path)
+    rows = [ln.split() for ln in golden5.read_text().splitlines() if ln and not ln.startswith("#")]
+    byg = {}
+    for r in rows:
+        byg.setdefault(int(r[0]), []).append(r)
+    strict = q.Context(0, threshold=1e-12)
+    gs, ogs = q.enumerate_graphs(5), o_enum(5)
+    n = 0
+    for gi, rs in sorted(byg.items()):
+        if _name(ogs[gi]) not in progs:
+            continue
+        d = strict.load(gs[gi])
+        assert d.n_lines == 15
+        zs, fs, lps, fls = [], [], [], []
+        for r in rs:
+            z, f, lp, fl = d.dump_points(int(r[1]), 1, seed=0)
+            zs.append(z.cpu().numpy()[0]); fs.append(f.item()); lps.append(lp.item()); fls.append(fl.item())
+        zo = np.array([[float(v) for v in r[3:18]] for r in rs])
+        lpo = np.array([float(r[2]) for r in rs])
+        fo = np.array([float(np.longdouble(r[18])) for r in rs])
+        np.testing.assert_allclose(np.array(zs), zo, rtol=1e-12, atol=0)
+        np.testing.assert_allclose(lps, lpo, rtol=1e-12, atol=1e-12)
+        ok = np.array(fls) == 0
+        rel = np.abs(np.array(fs) - fo) / np.abs(fo)
+        assert np.all(rel[ok] < 1e-12), (gi, rel[ok])
+        fdd = d.eval_points(torch.tensor(zo, device="cuda"), prec=1).cpu().numpy()
+        rdd = np.abs(fdd - fo) / np.abs(fo)
+        if np.any(rdd > 1e-12):
+            fp, W = interpret(progs[_name(ogs[gi])], zo, np.longdouble)
+            kappa = (W / np.abs(fp)).astype(np.float64)
+            assert np.all(rdd <= 1e-12 + 16 * 2.0 ** -64 * kappa), (gi, rdd, kappa)
+        n += len(rs)
+        d.close()
+    if n == 0:
+        pytest.skip("no stored five-loop graph has a generated program")
+    print(f"five-loop points: {n} double-double values at 1e-12")

@@ -183,3 +183,35 @@ def test_four_loop_programs_match_stored_oracle():
         kappa = (W / np.abs(fv)).astype(float)
         rel = np.abs((fv - fo) / fo).astype(float)
         assert np.all(rel <= 1e-12 + 16 * 2.0 ** -64 * kappa), (gi, rel, kappa)
+
+
+def test_five_loop_programs_match_stored_oracle():
+    """The generator's five-loop programs in long double against the
+    oracle's stored five-loop values (tests/golden/five_loop_points.txt),
+    for the stored graphs whose programs were generated (five-loop programs
+    are built on request)."""
+    path = GEN / "vm_n5.bin.z"
+    golden5 = ROOT / "tests" / "golden" / "five_loop_points.txt"
+    if not path.exists() or not golden5.exists():
+        pytest.skip("five-loop programs or stored points missing")
+    progs = read_programs(path)
+    gs = o_enum(5)
+    byg = {}
+    for ln in golden5.read_text().splitlines():
+        if ln and not ln.startswith("#"):
+            r = ln.split()
+            byg.setdefault(int(r[0]), []).append(r)
+    n = 0
+    for gi, rs in sorted(byg.items()):
+        p = progs.get(_name(gs[gi]))
+        if p is None:
+            continue
+        z = np.array([[float(v) for v in r[3:18]] for r in rs])
+        fo = np.array([np.longdouble(r[18]) for r in rs])
+        fv, W = interpret(p, z, np.longdouble)
+        kappa = (W / np.abs(fv)).astype(float)
+        rel = np.abs((fv - fo) / fo).astype(float)
+        assert np.all(rel <= 1e-12 + 16 * 2.0 ** -64 * kappa), (gi, rel, kappa)
+        n += len(rs)
+    if n == 0:
+        pytest.skip("no stored five-loop graph has a generated program")
