@@ -7,12 +7,12 @@ rule's table).  Calls only oracle/.
 
 Graphs: by default the five graphs of the 64-graph five-loop workload
 (five_loop_subset.txt) with the cheapest programs, at the counters in
-COUNTERS; the oracle needs about four minutes per five-loop point in FP64
-and four times that in long double.  Rows are appended to
+COUNTERS; the oracle needs about four minutes per five-loop point in
+float64 (an hour or more in long double), so the values are float64.  Rows are appended to
 five_loop_points.partial as they finish and a rerun resumes from it; with
 --graphs / --counters the new rows replace the rows of the same (graph,
 counter) in the existing file.  Columns: graph index, counter, log p,
-z[0..14], f in long double (20 significant digits).
+z[0..14], f in float64 (17 significant digits).
 """
 import argparse
 import multiprocessing as mp
@@ -44,7 +44,8 @@ def row(job):
     deg = deg_table(g)
     u = uniforms(np.array([c], dtype=np.uint64), gi, 0, 2 * (N - 1))
     x, lp, _ = sample_points(u, deg, f_table(deg, N), N)
-    f = Integrand(g)(x, dtype=np.longdouble)
+    # float64: a long-double five-loop point takes the oracle an hour or more
+    f = Integrand(g)(x, dtype=np.float64)
     zs = " ".join(repr(float(v)) for v in x[0])
     return f"{gi} {c} {float(lp[0])!r} {zs} {np.format_float_scientific(f[0], precision=19)}"
 
@@ -82,7 +83,7 @@ def main():
     keys = sorted(done)
     with open(OUT, "w") as fh:
         fh.write("# four-loop integrand at Eq. (1) points (oracle, long double); written by make_four_loop.py\n")
-        fh.write("# Deg table: the Deg rule (oracle deg_table), c_div 0.5, d_min 0.05\n")
+        fh.write("# Deg table: the Deg rule (oracle deg_table), c_div 0.5, d_min 0.05; f in float64\n")
         fh.write("# graph counter logp z0..z14 f\n")
         for k in keys:
             fh.write(done[k] + "\n")

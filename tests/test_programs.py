@@ -187,9 +187,10 @@ def test_four_loop_programs_match_stored_oracle():
 
 def test_five_loop_programs_match_stored_oracle():
     """The generator's five-loop programs in long double against the
-    oracle's stored five-loop values (tests/golden/five_loop_points.txt),
-    for the stored graphs whose programs were generated (five-loop programs
-    are built on request)."""
+    oracle's stored five-loop values (tests/golden/five_loop_points.txt,
+    float64: within 1e-12 plus 16 x 2^-53 x kappa), for the stored graphs
+    whose programs were generated (five-loop programs are built on
+    request)."""
     path = GEN / "vm_n5.bin.z"
     golden5 = ROOT / "tests" / "golden" / "five_loop_points.txt"
     if not path.exists() or not golden5.exists():
@@ -207,11 +208,11 @@ def test_five_loop_programs_match_stored_oracle():
         if p is None:
             continue
         z = np.array([[float(v) for v in r[3:18]] for r in rs])
-        fo = np.array([np.longdouble(r[18]) for r in rs])
+        fo = np.array([np.longdouble(float(r[18])) for r in rs])
         fv, W = interpret(p, z, np.longdouble)
         kappa = (W / np.abs(fv)).astype(float)
         rel = np.abs((fv - fo) / fo).astype(float)
-        assert np.all(rel <= 1e-12 + 16 * 2.0 ** -64 * kappa), (gi, rel, kappa)
+        assert np.all(rel <= 1e-12 + 16 * 2.0 ** -53 * kappa), (gi, rel, kappa)
         n += len(rs)
     if n == 0:
         pytest.skip("no stored five-loop graph has a generated program")
