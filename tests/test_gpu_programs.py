@@ -275,11 +275,14 @@ def test_four_loop_estimate_bounds_accepted_error(thresh):
 def test_five_loop_points_match_oracle():
     """Five loops (15 lines) against the oracle's own integrand: at the
     oracle's stored points (tests/golden/five_loop_points.txt, float64,
-    written from oracle/ alone) the GPU's points and log p to 1e-12, and its
-    accepted FP64 values (threshold 1e-12) and double-double values to 1e-12
-    plus the float64 oracle's own rounding (16 x 2^-53 x kappa of the graph's
-    program at that point), for the stored graphs whose programs were
-    generated."""
+    written from oracle/ alone) the GPU's points and log p to 1e-12; where
+    the integrand is well conditioned (kappa = sum |monomials| / |f| <= 1e4,
+    which every value accepted at the threshold 1e-12 is) its accepted FP64
+    values and its double-double values to 1e-12 plus the float64 oracle's
+    own rounding (16 x 2^-53 x kappa); at the strongly cancelling points,
+    where the float64 oracle has lost the digits, the double-double values
+    against the program in long double on the CPU (1e-12 plus 16 x 2^-64 x
+    kappa).  For the stored graphs whose programs were generated."""
     _need_gpu()
     golden5 = ROOT / "tests" / "golden" / "five_loop_points.txt"
     path = ROOT / "paper_1905_08007_b300" / "csrc" / "_gen" / "vm_n5.bin.z"
@@ -310,13 +313,19 @@ def test_five_loop_points_match_oracle():
         np.testing.assert_allclose(np.array(zs), zo, rtol=1e-12, atol=0)
         np.testing.assert_allclose(lps, lpo, rtol=1e-12, atol=1e-12)
         fp, W = interpret(progs[_name(ogs[gi])], zo, np.longdouble)
-        allow = 1e-12 + 16 * 2.0 ** -53 * (W / np.abs(fp)).astype(np.float64)
+        kappa = (W / np.abs(fp)).astype(np.float64)
+        good = kappa <= 1e4
+        allow = 1e-12 + 16 * 2.0 ** -53 * kappa
         ok = np.array(fls) == 0
+        assert np.all(good[ok])
         rel = np.abs(np.array(fs) - fo) / np.abs(fo)
         assert np.all(rel[ok] < allow[ok]), (gi, rel[ok], allow[ok])
         fdd = d.eval_points(torch.tensor(zo, device="cuda"), prec=1).cpu().numpy()
         rdd = np.abs(fdd - fo) / np.abs(fo)
-        assert np.all(rdd <= allow), (gi, rdd, allow)
+        assert np.all(rdd[good] <= allow[good]), (gi, rdd, allow)
+        fpd = fp.astype(np.float64)
+        rp = np.abs(fdd - fpd) / np.abs(fpd)
+        assert np.all(rp[~good] <= 1e-12 + 16 * 2.0 ** -64 * kappa[~good]), (gi, rp, kappa)
         n += len(rs)
         d.close()
     if n == 0:
