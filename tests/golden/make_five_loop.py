@@ -5,11 +5,12 @@ rule's table).  Calls only oracle/.
 
     python tests/golden/make_five_loop.py [--procs 4] [--graphs G ...] [--counters C ...]
 
-Graphs: by default the five graphs of the 64-graph five-loop workload
-(five_loop_subset.txt) with the cheapest programs, at the counters in
-COUNTERS; the oracle needs about four minutes per five-loop point in
-float64 (an hour or more in long double), so the values are float64.  Rows are appended to
-five_loop_points.partial as they finish and a rerun resumes from it; with
+Graphs: by default five graphs of the 64-graph five-loop workload
+(five_loop_subset.txt) whose programs take the generator a few minutes, at
+the counters in COUNTERS; the oracle needs about four minutes per
+five-loop point in float64 (an hour or more in long double), so the values
+are float64.  Rows are appended to five_loop_points.partial as they finish
+and a rerun resumes from it; with
 --graphs / --counters the new rows replace the rows of the same (graph,
 counter) in the existing file.  Columns: graph index, counter, log p,
 z[0..14], f in float64 (17 significant digits).
@@ -82,7 +83,7 @@ def main():
     done = keep
     keys = sorted(done)
     with open(OUT, "w") as fh:
-        fh.write("# four-loop integrand at Eq. (1) points (oracle, long double); written by make_four_loop.py\n")
+        fh.write("# five-loop integrand at Eq. (1) points (oracle, float64); written by make_five_loop.py\n")
         fh.write("# Deg table: the Deg rule (oracle deg_table), c_div 0.5, d_min 0.05; f in float64\n")
         fh.write("# graph counter logp z0..z14 f\n")
         for k in keys:
