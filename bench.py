@@ -385,7 +385,10 @@ def run_native(args):
             ddflops.append(d.flops_per_dd_sample())
         except q.QedError:
             ddflops.append(None)
-    rounds, chunk = 4, int(args.chunk or CHUNK[args.order])
+    # allocation rounds per step: round 0 equal, the others by running
+    # variance; every round ends with the tail of its double-double pass,
+    # so fewer, larger rounds waste less (three at four loops)
+    rounds, chunk = args.rounds, int(args.chunk or CHUNK[args.order])
 
     def step(s):
         base = (s * ws + rank) * total + (1 << 40)      # fresh counters every step and rank
@@ -478,7 +481,7 @@ def run_native(args):
                                    else "gradient-tuned Deg-rule densities"))
                                + f", forest-subtracted FP64 integrand, double-double re-evaluation above "
                                f"{args.threshold:g}, "
-                               "persistent batched kernel (4 CUDA-graph rounds per step)",
+                               f"persistent batched kernel ({rounds} CUDA-graph rounds per step)",
                    "loops": args.order, "graphs": len(graphs), "samples_per_step": total, "seed": args.seed, "l2_flush": True,
                    "flag_threshold": args.threshold, "deg": "calibrated" if args.calibrate else "rule",
                    "rng": {"philox": "Philox4x32-10 (Calc 2)", "mrg32k3a": "MRG32k3a (Calc 1)"}[args.rng],
@@ -547,6 +550,8 @@ def main(argv=None):
     ap.add_argument("--order", type=int, default=4, choices=[1, 2, 3, 4, 5], help="loop order of the graph set")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=None, help="samples per work item of the batched kernel")
+    ap.add_argument("--rounds", type=int, default=None,
+                    help="allocation rounds per step (default 3 at four loops, else 4)")
     ap.add_argument("--threshold", type=float, default=1e-6,
                     help="relative rounding-error threshold above which a point is re-evaluated in "
                          "double-double: at four loops every accepted point was measured within 0.21 x the "
@@ -570,6 +575,8 @@ def main(argv=None):
         a.warmup = 3
     if a.calibrate is None:
         a.calibrate = a.order <= 3
+    if a.rounds is None:
+        a.rounds = 3 if a.order == 4 else 4
     if a.impl == "reference":
         return run_reference(a)
     return run_native(a)
