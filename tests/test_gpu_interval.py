@@ -16,7 +16,6 @@ the C ABI.
   in interval arithmetic and the rest re-evaluated in double-double gives,
   on the same samples, the estimate rule's value within the thresholds.
 """
-import math
 from pathlib import Path
 
 import numpy as np
