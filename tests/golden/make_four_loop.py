@@ -62,6 +62,8 @@ def main():
     ap.add_argument("--procs", type=int, default=6)
     ap.add_argument("--graphs", type=int, nargs="*", default=None)
     ap.add_argument("--counters", type=int, nargs="*", default=None)
+    ap.add_argument("--merge-only", action="store_true",
+                    help="write the rows finished so far (the .partial file) into the file and stop")
     a = ap.parse_args()
     gis = a.graphs if a.graphs else graphs()
     counters = a.counters if a.counters else COUNTERS
@@ -77,7 +79,7 @@ def main():
             p = ln.split()
             if len(p) == 16:
                 done[(int(p[0]), int(p[1]))] = ln
-    jobs = [(gi, c) for gi in gis for c in counters if (gi, c) not in done]
+    jobs = [] if a.merge_only else [(gi, c) for gi in gis for c in counters if (gi, c) not in done]
     ctx = mp.get_context("spawn")
     with ctx.Pool(a.procs) as pool, open(PARTIAL, "a") as fh:
         for ln in pool.imap_unordered(row, jobs):
@@ -85,6 +87,11 @@ def main():
             fh.flush()
             p = ln.split()
             done[(int(p[0]), int(p[1]))] = ln
+    if a.merge_only and OUT.exists():
+        for ln in OUT.read_text().splitlines():
+            p = ln.split()
+            if len(p) == 16 and not ln.startswith("#"):
+                keep.setdefault((int(p[0]), int(p[1])), ln)
     keep.update(done)
     done = keep
     keys = sorted(done)

